@@ -1,0 +1,230 @@
+/*
+ * cfd.h -- C ABI of the GB300 ChebFD library (libcfd.so).
+ *
+ * Chebyshev filter diagonalization (ChebFD) after Kreutzer et al.,
+ * "Chebyshev Filter Diagonalization on Modern Manycore Processors and GPGPUs"
+ * (arxiv 1803.02156): the block polynomial filter
+ *     X <- sum_{k=0}^{n_p} g_k c_k T_k(H~) X,   H~ = alpha (H - beta 1),
+ * applied to n_s search vectors in subspace blocks of n_b vectors (Algorithms
+ * 1 and 2), on a sparse complex Hermitian matrix H stored in SELL-C-sigma.
+ *
+ * Conventions shared by every entry point
+ *   - Plain C types and pointers only.  "device" pointers are CUDA global
+ *     memory on the current device; "host" pointers are ordinary CPU memory.
+ *   - The caller allocates all memory.  The library never calls cudaMalloc
+ *     or cudaFree; sizes come from the *_size / *_workspace queries.  Buffers
+ *     must stay alive until the work queued on the stream has finished.
+ *   - All GPU work is queued on the caller's stream.  Entry points that return
+ *     host results say so and synchronise that stream only.
+ *   - Every call returns a cfd_status.  Nothing aborts or throws across the
+ *     ABI.  On failure cfd_last_error() returns a message for the calling
+ *     thread.  CUDA errors of earlier asynchronous work may surface at the
+ *     next call that checks the stream (reported as CFD_ERR_CUDA).
+ *   - Complex scalars are interleaved (re, im): 16 bytes for CFD_C128, 8 bytes
+ *     for CFD_C64.  Block vectors are row-major ("interleaved", Sect. 3.1):
+ *     element (i, j) of a block sits at ptr + (i * ld + j) * scalar size.
+ *   - Device pointers must be 16-byte aligned; ld * scalar size must be a
+ *     multiple of 16 bytes.
+ */
+#ifndef CFD_H
+#define CFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cfd_status {
+    CFD_OK = 0,
+    CFD_ERR_ARG = 1,      /* invalid argument (sizes, alignment, window, NULL) */
+    CFD_ERR_CUDA = 2,     /* a CUDA runtime call or kernel launch failed */
+    CFD_ERR_OOM = 3,      /* the caller's workspace is smaller than required */
+    CFD_ERR_BOUNDS = 4,   /* spectrum of H~ left [-1, 1]: moments grew */
+    CFD_ERR_TIMEOUT = 5,  /* a bounded device-side wait expired */
+    CFD_ERR_NOCONV = 6,   /* the solve hit max_iter without converging */
+    CFD_ERR_INTERNAL = 7  /* internal inconsistency */
+} cfd_status;
+
+typedef enum cfd_prec {
+    CFD_C128 = 0,         /* complex double: fp64 arithmetic */
+    CFD_C64 = 1           /* complex float: fp32 arithmetic and accumulation */
+} cfd_prec;
+
+/* Human-readable name of a status code (static string). */
+const char *cfd_status_string(int status);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *cfd_last_error(void);
+
+/* Library version, e.g. "1.0.0" (static string). */
+const char *cfd_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Matrix: the topological-insulator Hamiltonian in SELL-C-sigma             */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Parameters of Topi-Nx-Ny-Nz (Sect. 2.1, "Physical Application and Problem
+ * Setting"): a lattice of Nx x Ny x Nz sites with four orbitals each,
+ * n = 4 Nx Ny Nz rows, row = 4 site + orbital, site = x + Nx (y + Ny z).
+ *   on-site block (m + V_s) Gamma_1, V_s = gamma (u_s - 1/2), u_s uniform in
+ *     [0, 1) from counter-based SplitMix64 (seed, stream tag 0, index s);
+ *   hop block T_j = -(t/2) Gamma_1 + i (t/2) Gamma_{j+2} at block
+ *     (site + e_j, site) and T_j^H at (site, site + e_j);
+ *   Gamma_1 = s_z (x) 1, Gamma_{2,3,4} = s_x (x) s_{x,y,z}, index 2a + b;
+ *   axis j wraps when periodic_j != 0, else it is open.
+ * 13 nonzeros per interior row.  Periodic axes need at least 3 sites.
+ */
+typedef struct cfd_topi_params {
+    int32_t Nx, Ny, Nz;
+    int32_t periodic_x, periodic_y, periodic_z;
+    double t, m, gamma;
+    uint64_t seed;
+} cfd_topi_params;
+
+/* Sizes (bytes) of the caller-allocated arrays of a SELL-C-sigma matrix. */
+typedef struct cfd_matrix_sizes {
+    int64_t n_rows;          /* N */
+    int64_t nnz;             /* stored nonzeros of the canonical matrix */
+    int64_t n_chunks;        /* ceil(N / C) */
+    int64_t n_slots;         /* sum over chunks of C * chunk length (>= nnz) */
+    int64_t bytes_val;       /* n_slots complex scalars */
+    int64_t bytes_col;       /* n_slots int32 */
+    int64_t bytes_chunk_ptr; /* (n_chunks + 1) int64 */
+    int64_t bytes_chunk_len; /* n_chunks int32 */
+    int64_t bytes_perm;      /* N int32 when sigma > 1, else 0 */
+    int64_t bytes_work;      /* build scratch, free again when the build ends */
+} cfd_matrix_sizes;
+
+/* Caller-allocated device buffers for cfd_build_matrix (sizes above). */
+typedef struct cfd_matrix_buffers {
+    void *val, *col, *chunk_ptr, *chunk_len, *perm, *work;
+} cfd_matrix_buffers;
+
+/*
+ * A SELL-C-sigma matrix (Kreutzer et al. 2014, cited as the GHOST format).
+ * Rows are taken in windows of sigma rows, sorted by decreasing length inside
+ * each window (stable), and packed into chunks of C consecutive sorted rows.
+ * Chunk c holds chunk_len[c] slots per row, stored slot-major: slot k of
+ * sorted row r (r = c C + rr) sits at chunk_ptr[c] + k C + rr.  Within a row
+ * the slots are in ascending column order; padding slots have col = -1 and
+ * value 0.  Sorted row r is canonical row perm[r] (perm == NULL when
+ * sigma == 1).  Column indices are canonical.  The struct only points into
+ * caller memory.
+ */
+typedef struct cfd_matrix {
+    int64_t n_rows, nnz, n_chunks, n_slots;
+    int32_t C, sigma, prec, reserved;
+    void *val;
+    int32_t *col;
+    int64_t *chunk_ptr;
+    int32_t *chunk_len;
+    int32_t *perm;
+} cfd_matrix;
+
+/*
+ * Sizes of the arrays cfd_build_matrix needs for Topi with chunk height C
+ * (power of two, 4..128), sorting window sigma (1, or a multiple of C up to
+ * 65536) and value precision prec.  Host-only; no GPU work.
+ * Errors: CFD_ERR_ARG for invalid lattice, C, sigma or prec.
+ */
+cfd_status cfd_matrix_query_size(const cfd_topi_params *p, int C, int sigma, int prec,
+                                 cfd_matrix_sizes *out);
+
+/*
+ * Build Topi (parameters p, see above) in SELL-C-sigma into the caller's
+ * device buffers, on `stream`.  Values are computed in fp64 exactly as
+ * defined (one rounding each for gamma (u - 1/2) and m + V) and rounded to
+ * float for CFD_C64.  Fills *out (host struct) with the metadata and pointers.
+ * Asynchronous.  Errors: CFD_ERR_ARG (parameters, NULL or misaligned
+ * buffers), CFD_ERR_CUDA (launch failure).
+ */
+cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec,
+                            const cfd_matrix_buffers *buf, cfd_matrix *out, cudaStream_t stream);
+
+/* Device scratch bytes cfd_matrix_export_csr needs. */
+size_t cfd_export_csr_workspace(const cfd_matrix *H);
+
+/*
+ * Export H as canonical CSR (rows in lattice order, columns ascending,
+ * padding dropped) into device arrays rowptr[N + 1] (int64), col[nnz]
+ * (int32) and val[nnz] (complex of H's precision).  Asynchronous.
+ */
+cfd_status cfd_matrix_export_csr(const cfd_matrix *H, int64_t *rowptr, int32_t *col, void *val,
+                                 void *work, size_t work_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* The ChebFD polynomial filter                                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Filter weights gc[k] = g_k c_k, k = 0..n_p, written to device memory
+ * (n_p + 1 doubles).  H~ = alpha (H - beta), alpha = 2 / (lmax - lmin),
+ * beta = (lmax + lmin) / 2 maps [lmin, lmax] onto [-1, 1] (the map
+ * alpha H + beta 1 of Algorithm 1 with the paper's beta written as
+ * -alpha beta).  c_k are the Chebyshev coefficients of the indicator of the
+ * search interval [lam_l, lam_r]: with theta = arccos(alpha (lam - beta)),
+ * c_0 = (theta_l - theta_r) / pi, c_k = 2 (sin k theta_l - sin k theta_r) / (k pi);
+ * g_k is the Jackson kernel for M = n_p + 1 moments,
+ * g_k = [(M - k + 1) cos(pi k / (M + 1)) + sin(pi k / (M + 1)) cot(pi / (M + 1))] / (M + 1).
+ * (The paper names c_k, g_k and the window in Sect. 2 and Algorithm 1 and
+ * defers their definition to its references.)  Asynchronous.
+ * Errors: CFD_ERR_ARG unless lmin <= lam_l < lam_r <= lmax, lmin < lmax, n_p >= 2.
+ */
+cfd_status cfd_filter_coeffs(double lmin, double lmax, double lam_l, double lam_r, int n_p,
+                             double *gc, cudaStream_t stream);
+
+/* A row-major block of n_cols complex vectors of length n_rows. */
+typedef struct cfd_block {
+    void *ptr;        /* device pointer */
+    int64_t n_rows;   /* N */
+    int64_t ld;       /* row stride in scalars, >= n_cols */
+    int32_t n_cols;   /* n_s */
+    int32_t prec;     /* cfd_prec */
+} cfd_block;
+
+/*
+ * Device scratch bytes cfd_filter needs for an N x n_s block filtered in
+ * blocks of n_b vectors with degree n_p, matrix precision prec_H and block
+ * precision prec_X.
+ */
+size_t cfd_filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X);
+
+/*
+ * Apply the ChebFD filter to X in place (Algorithm 1, blocked as Algorithm
+ * 2): for each block b of n_b columns [b n_b, (b + 1) n_b),
+ *   V1 = H~ X_b;  V2 = 2 H~ V1 - X_b;  X_b <- gc0 X_b + gc1 V1 + gc2 V2;
+ *   for p = 3..n_p: swap(V_prev, V_cur); V_prev <- 2 H~ V_cur - V_prev;
+ *                   eta_p = Re <V_prev, V_cur>; mu_p = <V_cur, V_cur>;
+ *                   X_b <- X_b + gc_p V_prev,
+ * each step one fused kernel (the paper's chebfd_op) over the SELL-C-sigma
+ * matrix.  H~ and gc as in cfd_filter_coeffs.
+ *
+ * Precision: X.prec == H->prec runs entirely in that precision.  H->prec ==
+ * CFD_C64 with X.prec == CFD_C128 is the mixed mode: each block is rounded to
+ * complex float (round to nearest), filtered in fp32 with fp32 accumulation,
+ * and widened back.
+ *
+ * moments (device, nullable): [n_s][2 n_p] doubles, the Chebyshev moments
+ * mu_m = <x_j, T_m(H~) x_j>, m = 0..2 n_p - 1, of the input columns, from the
+ * per-step dot products (lines 10-11 of Algorithm 1, plus the same dots on
+ * the two seed steps) via T_k T_l = (T_{k+l} + T_{|k-l|}) / 2.  The
+ * reductions are deterministic (fixed order).
+ *
+ * work: device scratch of cfd_filter_workspace(...) bytes.  n_b must divide
+ * n_s and be one of 8, 16, 32, 64.  Asynchronous.
+ * Errors: CFD_ERR_ARG (sizes, window, precision pair, alignment),
+ * CFD_ERR_OOM (work too small), CFD_ERR_CUDA.
+ */
+cfd_status cfd_filter(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                      int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
+                      double *moments, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFD_H */

@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libcfd.so (include/cfd.h).
+
+Argument marshalling only: torch supplies device memory and the current CUDA
+stream, every computation runs in the library's kernels.  Function names
+match the C ABI.  There is no fallback: if the library is missing or no GPU
+is present the calls raise.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcfd.so")
+
+CFD_C128, CFD_C64 = 0, 1
+PREC = {"c128": CFD_C128, "c64": CFD_C64}
+TORCH_DTYPE = {CFD_C128: torch.complex128, CFD_C64: torch.complex64}
+SCALAR_BYTES = {CFD_C128: 16, CFD_C64: 8}
+
+STATUS = {0: "CFD_OK", 1: "CFD_ERR_ARG", 2: "CFD_ERR_CUDA", 3: "CFD_ERR_OOM", 4: "CFD_ERR_BOUNDS",
+          5: "CFD_ERR_TIMEOUT", 6: "CFD_ERR_NOCONV", 7: "CFD_ERR_INTERNAL"}
+
+
+class CfdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+# ------------------------------------------------------------ structs --
+
+class cfd_topi_params(ctypes.Structure):
+    _fields_ = [("Nx", ctypes.c_int32), ("Ny", ctypes.c_int32), ("Nz", ctypes.c_int32),
+                ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("periodic_z", ctypes.c_int32), ("t", ctypes.c_double), ("m", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class cfd_matrix_sizes(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_rows", "nnz", "n_chunks", "n_slots", "bytes_val", "bytes_col", "bytes_chunk_ptr",
+        "bytes_chunk_len", "bytes_perm", "bytes_work")]
+
+
+class cfd_matrix_buffers(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("val", "col", "chunk_ptr", "chunk_len", "perm", "work")]
+
+
+class cfd_matrix(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_chunks", ctypes.c_int64),
+                ("n_slots", ctypes.c_int64), ("C", ctypes.c_int32), ("sigma", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32), ("val", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("chunk_ptr", ctypes.c_void_p),
+                ("chunk_len", ctypes.c_void_p), ("perm", ctypes.c_void_p)]
+
+
+class cfd_block(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("n_rows", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("n_cols", ctypes.c_int32), ("prec", ctypes.c_int32)]
+
+
+# ---------------------------------------------------------------- load --
+
+_LIB = None
+
+_PROTOS = {
+    "cfd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cfd_last_error": (ctypes.c_char_p, []),
+    "cfd_version": (ctypes.c_char_p, []),
+    "cfd_matrix_query_size": (ctypes.c_int, [ctypes.POINTER(cfd_topi_params), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.POINTER(cfd_matrix_sizes)]),
+    "cfd_build_matrix": (ctypes.c_int, [ctypes.POINTER(cfd_topi_params), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(cfd_matrix_buffers),
+                                        ctypes.POINTER(cfd_matrix), ctypes.c_void_p]),
+    "cfd_export_csr_workspace": (ctypes.c_size_t, [ctypes.POINTER(cfd_matrix)]),
+    "cfd_matrix_export_csr": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.c_void_p]),
+    "cfd_filter_coeffs": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "cfd_filter_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int]),
+    "cfd_filter": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load libcfd.so (built in-tree by __graft_entry__.build())."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcfd.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def declared_symbols():
+    """Names of the entry points this binding expects the library to export."""
+    return sorted(_PROTOS)
+
+
+def _check(st):
+    if st != 0:
+        raise CfdError(st, lib().cfd_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def cfd_version():
+    return lib().cfd_version().decode()
+
+
+# -------------------------------------------------------------- matrix --
+
+def topi_params(Nx, Ny, Nz, t=1.0, m=2.0, gamma=1.0, seed=1, periodic=(1, 1, 0)):
+    return cfd_topi_params(Nx, Ny, Nz, int(periodic[0]), int(periodic[1]), int(periodic[2]),
+                           float(t), float(m), float(gamma), int(seed))
+
+
+def cfd_matrix_query_size(params, C=32, sigma=1, prec="c128"):
+    sz = cfd_matrix_sizes()
+    _check(lib().cfd_matrix_query_size(ctypes.byref(params), C, sigma, _prec(prec), ctypes.byref(sz)))
+    return sz
+
+
+class Matrix:
+    """A built SELL-C-sigma matrix: the C struct plus the torch buffers it points into."""
+
+    def __init__(self, cmat, buffers, params):
+        self.c = cmat
+        self.buffers = buffers
+        self.params = params
+
+    @property
+    def N(self):
+        return self.c.n_rows
+
+    @property
+    def nnz(self):
+        return self.c.nnz
+
+    @property
+    def prec(self):
+        return self.c.prec
+
+    def ref(self):
+        return ctypes.byref(self.c)
+
+
+def cfd_build_matrix(params, C=32, sigma=1, prec="c128", device="cuda", stream=None):
+    """Allocate the SELL-C-sigma buffers with torch and build Topi into them."""
+    prec = _prec(prec)
+    sz = cfd_matrix_query_size(params, C, sigma, prec)
+    dev = torch.device(device)
+    bufs = {
+        "val": _workspace(sz.bytes_val, dev), "col": _workspace(sz.bytes_col, dev),
+        "chunk_ptr": _workspace(sz.bytes_chunk_ptr, dev), "chunk_len": _workspace(sz.bytes_chunk_len, dev),
+        "perm": _workspace(sz.bytes_perm, dev) if sz.bytes_perm else None,
+        "work": _workspace(sz.bytes_work, dev),
+    }
+    b = cfd_matrix_buffers(*[(bufs[k].data_ptr() if bufs[k] is not None else None)
+                             for k in ("val", "col", "chunk_ptr", "chunk_len", "perm", "work")])
+    out = cfd_matrix()
+    _check(lib().cfd_build_matrix(ctypes.byref(params), C, sigma, prec, ctypes.byref(b), ctypes.byref(out),
+                                  _stream(stream)))
+    return Matrix(out, bufs, params)
+
+
+def cfd_matrix_export_csr(H, stream=None):
+    """Canonical CSR of H as torch device tensors (rowptr int64, col int32, val complex)."""
+    dev = H.buffers["val"].device
+    rowptr = torch.empty(H.N + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(H.nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(H.nnz, dtype=TORCH_DTYPE[H.prec], device=dev)
+    ws = lib().cfd_export_csr_workspace(H.ref())
+    work = _workspace(ws, dev)
+    _check(lib().cfd_matrix_export_csr(H.ref(), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(work), ws,
+                                       _stream(stream)))
+    return rowptr, col, val
+
+
+# -------------------------------------------------------------- filter --
+
+def cfd_filter_coeffs(lmin, lmax, lam_l, lam_r, n_p, device="cuda", stream=None):
+    gc = torch.empty(n_p + 1, dtype=torch.float64, device=device)
+    _check(lib().cfd_filter_coeffs(lmin, lmax, lam_l, lam_r, n_p, _ptr(gc), _stream(stream)))
+    return gc
+
+
+def block_of(X):
+    """cfd_block describing a 2-D torch complex tensor with unit column stride."""
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("block must be a 2-D tensor with unit column stride")
+    prec = {torch.complex128: CFD_C128, torch.complex64: CFD_C64}[X.dtype]
+    return cfd_block(X.data_ptr(), X.shape[0], X.stride(0), X.shape[1], prec)
+
+
+def cfd_filter_workspace(N, n_s, n_b, n_p, prec_H, prec_X):
+    return lib().cfd_filter_workspace(N, n_s, n_b, n_p, _prec(prec_H), _prec(prec_X))
+
+
+def cfd_filter(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=None, stream=None):
+    """Filter the columns of X (N x n_s complex, row-major) in place.  Returns the
+    [n_s, 2 n_p] Chebyshev moments (float64 device tensor) when moments=True."""
+    blk = block_of(X)
+    ws = cfd_filter_workspace(H.N, blk.n_cols, n_b, n_p, H.prec, blk.prec)
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, X.device)
+    mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=X.device) if moments else None
+    _check(lib().cfd_filter(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
+                            _ptr(mu), _stream(stream)))
+    return mu

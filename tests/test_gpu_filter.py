@@ -1,0 +1,177 @@
+"""GPU parity of the matrix build and the fused ChebFD filter against the CPU
+oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_02156_gb300 import inputs, workloads
+
+pytestmark = pytest.mark.gpu
+
+# filtered block vs oracle (relative Frobenius) and moments (relative to max |mu|), fp64 path
+TOL_C128 = 1e-11
+
+
+@pytest.fixture(scope="module")
+def b():
+    import torch
+    from paper_1803_02156_gb300 import build, binding
+    assert torch.cuda.is_available()
+    build.build()
+    binding.lib()
+    return binding
+
+
+def _gpu_block(X, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(X)).to(dtype).cuda()
+
+
+@pytest.mark.parametrize("L,per,C,sigma", [((8, 8, 8), (1, 1, 0), 32, 1), ((17, 23, 9), (1, 1, 0), 32, 64),
+                                           ((4, 4, 4), (1, 1, 1), 8, 1), ((5, 4, 6), (0, 1, 0), 16, 32),
+                                           ((3, 3, 1), (1, 1, 0), 4, 1)])
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_matrix_build_bitexact(b, L, per, C, sigma, prec):
+    import torch
+    p = b.topi_params(*L, seed=17, periodic=per)
+    H = b.cfd_build_matrix(p, C, sigma, prec)
+    rowptr, col, val = b.cfd_matrix_export_csr(H)
+    torch.cuda.synchronize()
+    ref = oracle.topi_csr(*L, seed=17, periodic=per)
+    assert np.array_equal(rowptr.cpu().numpy(), ref.rowptr)
+    assert np.array_equal(col.cpu().numpy(), ref.col)
+    v = val.cpu().numpy()
+    want = ref.val if prec == "c128" else ref.val.astype(np.complex64)
+    assert np.array_equal(v.view(np.uint8), want.view(np.uint8))           # bit-exact
+
+
+def test_filter_coeffs_match_oracle(b):
+    for (lmin, lmax, wl, wr, n_p) in [(-8.5, 8.5, -0.7, 0.7, 200), (-3.0, 5.0, 1.0, 1.5, 1000), (-1, 1, -1, 1, 10)]:
+        gc = b.cfd_filter_coeffs(lmin, lmax, wl, wr, n_p).cpu().numpy()
+        ref = oracle.filter_coeffs(wl, wr, lmin, lmax, n_p)
+        assert np.max(np.abs(gc - ref)) < 1e-14
+
+
+def _compare_filter(b, L, n_s, n_b, n_p, win, prec="c128", seed=1, tol=TOL_C128, bounds=(-8.6, 8.6)):
+    import torch
+    H = b.cfd_build_matrix(b.topi_params(*L, seed=seed), 32, 1, prec)
+    ref = oracle.topi_csr(*L, seed=seed)
+    X = inputs.gaussian_block(ref.N, n_s, seed=2)
+    Xg = _gpu_block(X, torch.complex128 if prec == "c128" else torch.complex64)
+    mu = b.cfd_filter(H, bounds[0], bounds[1], win[0], win[1], n_p, Xg, n_b, moments=True)
+    torch.cuda.synchronize()
+    Y, dots = oracle.chebfd_filter(ref, bounds[0], bounds[1], win[0], win[1], n_p, X, n_b)
+    Yg = Xg.cpu().numpy().astype(np.complex128)
+    err = np.linalg.norm(Yg - Y) / np.linalg.norm(Y)
+    muref = oracle.kpm_moments(dots)
+    merr = np.max(np.abs(mu.cpu().numpy() - muref)) / np.max(np.abs(muref))
+    assert err < tol, err
+    assert merr < tol, merr
+    return Xg, err, merr
+
+
+@pytest.mark.parametrize("n_b", [8, 16, 32])
+def test_filter_parity_small_config(b, n_b):
+    """8x8x8 (N = 2048), n_s = 32, n_p = 200: block and moments vs oracle."""
+    w = workloads.SMALL
+    _compare_filter(b, w.lattice, w.n_s, n_b, w.n_p, (-0.7, 0.7))
+
+
+@pytest.mark.parametrize("L,n_s,n_b,n_p", [((16, 16, 9), 64, 64, 40), ((13, 7, 5), 48, 16, 25),
+                                           ((9, 10, 3), 8, 8, 2)])
+def test_filter_parity_ragged(b, L, n_s, n_b, n_p):
+    """Several chunks and a ragged tail (N not a multiple of C or of the CTA's rows)."""
+    _compare_filter(b, L, n_s, n_b, n_p, (-1.1, 0.4))
+
+
+def test_filter_block_width_invariance(b):
+    """The fp64 filtered block is bitwise identical for every n_b."""
+    import torch
+    L = (12, 10, 7)
+    H = b.cfd_build_matrix(b.topi_params(*L), 32, 1, "c128")
+    X = inputs.gaussian_block(4 * 12 * 10 * 7, 64, seed=4)
+    outs = []
+    for n_b in (8, 16, 32, 64):
+        Xg = _gpu_block(X, torch.complex128)
+        b.cfd_filter(H, -8.6, 8.6, -0.5, 0.5, 60, Xg, n_b)
+        outs.append(Xg.cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_filter_deterministic_moments(b):
+    import torch
+    L = (16, 16, 8)
+    H = b.cfd_build_matrix(b.topi_params(*L), 32, 1, "c128")
+    X = inputs.gaussian_block(4 * 16 * 16 * 8, 32, seed=5)
+    res = []
+    for _ in range(2):
+        Xg = _gpu_block(X, torch.complex128)
+        mu = b.cfd_filter(H, -8.6, 8.6, -0.5, 0.5, 30, Xg, 32, moments=True)
+        res.append((Xg.cpu().numpy(), mu.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_filter_full_window_is_identity(b):
+    import torch
+    L = (8, 8, 4)
+    H = b.cfd_build_matrix(b.topi_params(*L), 32, 1, "c128")
+    X = inputs.gaussian_block(4 * 8 * 8 * 4, 16, seed=6)
+    Xg = _gpu_block(X, torch.complex128)
+    b.cfd_filter(H, -9.0, 9.0, -9.0, 9.0, 100, Xg, 16)
+    assert np.linalg.norm(Xg.cpu().numpy() - X) / np.linalg.norm(X) < 1e-13
+
+
+# fp32 arithmetic: the rounding of each step is about nnzr * u32 relative and
+# the three-term recurrence adds it up linearly over the n_p steps, so the
+# filtered block of the n_p = 200 configuration is within n_p * 13 * 2^-24
+# (1.6e-4) of the fp64 oracle; moments likewise.
+TOL_C64_200 = 200 * 13 * 2.0 ** -24
+
+
+def test_filter_c64_small_config(b):
+    w = workloads.SMALL
+    _compare_filter(b, w.lattice, w.n_s, 32, w.n_p, (-0.7, 0.7), prec="c64", tol=TOL_C64_200)
+
+
+def test_filter_mixed_precision_block(b):
+    """c64 matrix with a c128 block: narrowed, filtered in fp32, widened."""
+    import torch
+    w = workloads.SMALL
+    H = b.cfd_build_matrix(b.topi_params(*w.lattice), 32, 1, "c64")
+    ref = oracle.topi_csr(*w.lattice)
+    X = inputs.gaussian_block(ref.N, 32, seed=2)
+    Xg = _gpu_block(X, torch.complex128)
+    b.cfd_filter(H, -8.6, 8.6, -0.7, 0.7, 200, Xg, 16)
+    Y, _ = oracle.chebfd_filter(ref, -8.6, 8.6, -0.7, 0.7, 200, X, 16)
+    err = np.linalg.norm(Xg.cpu().numpy() - Y) / np.linalg.norm(Y)
+    assert err < TOL_C64_200, err
+
+
+def test_filter_parity_full_size_few_steps(b):
+    """The 64x64x32 lattice (N = 524288) in the bench's launch configuration
+    (n_b = 32, SELL C = 32, sigma = 1) for a few steps, against the oracle."""
+    w = workloads.MEDIUM
+    _compare_filter(b, w.lattice, 32, 32, 6, (-0.3, 0.3))
+
+
+def test_filter_full_size_properties(b):
+    """Full degree n_p = 1000 on 64x64x32: properties that hold at any size.
+    mu_0 = ||x||^2 and |mu_m| <= mu_0 (|T_m| <= 1 on the scaled spectrum);
+    the Jackson-damped filter has 0 <= p <= 1 on the spectrum, so no column
+    grows; the result is bitwise independent of n_b."""
+    import torch
+    w = workloads.MEDIUM
+    H = b.cfd_build_matrix(b.topi_params(*w.lattice), 32, 1, "c128")
+    X = inputs.gaussian_block(w.N, 64, seed=2)
+    outs = []
+    for n_b in (32, 64):
+        Xg = _gpu_block(X, torch.complex128)
+        mu = b.cfd_filter(H, -8.6, 8.6, -0.3, 0.3, w.n_p, Xg, n_b, moments=True)
+        outs.append(Xg.cpu().numpy())
+    mu = mu.cpu().numpy()
+    n0 = np.linalg.norm(X, axis=0) ** 2
+    assert np.allclose(mu[:, 0], n0, rtol=1e-12)
+    assert np.all(np.abs(mu) <= mu[:, :1] * (1 + 1e-9))
+    assert np.all(np.linalg.norm(outs[0], axis=0) ** 2 <= n0 * (1 + 1e-9))
+    assert np.array_equal(outs[0], outs[1])
