@@ -223,6 +223,36 @@ cfd_status cfd_filter(const cfd_matrix *H, double lmin, double lmax, double lam_
                       int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
                       double *moments, cudaStream_t stream);
 
+/* Size of the library-owned device scratch used by cfd_filter_noalloc. */
+#define CFD_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/*
+ * cfd_filter without a workspace argument, for callers that are not allowed
+ * to allocate device memory: code running under a host application's memory
+ * budget or pool, where raw cudaMalloc is forbidden or the pool already holds
+ * the memory, and latency-critical loops that cannot pay for cudaMalloc and
+ * the device-wide synchronisation it implies.  (The paper has no counterpart;
+ * this is a library convenience.)
+ *
+ * Same arguments, results and errors as cfd_filter, minus work/work_bytes.
+ * The scratch is a 64 MiB array inside the library, one copy on every device
+ * that loads it, kept until the process exits.  Problems whose
+ * cfd_filter_workspace(...) exceeds CFD_NOALLOC_SCRATCH_BYTES are rejected
+ * with CFD_ERR_ARG (roughly N * n_b <= 1.9e6 for complex double blocks).
+ * Nothing is allocated: no cudaMalloc/cudaFree and no allocating library call.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current) and caches it; make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last
+ * call's contents (what must start at zero is cleared by each call), so
+ * calls that can overlap on the GPU -- on different streams, or from
+ * different host threads without ordering -- race and corrupt each other;
+ * serialise them on one stream.
+ */
+cfd_status cfd_filter_noalloc(const cfd_matrix *H, double lmin, double lmax, double lam_l,
+                              double lam_r, int n_p, cfd_block X, int n_b, double *moments,
+                              cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,9 @@ _PROTOS = {
     "cfd_filter": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "cfd_filter_noalloc": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block,
+                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -233,3 +236,17 @@ def cfd_filter(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=Non
     _check(lib().cfd_filter(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
                             _ptr(mu), _stream(stream)))
     return mu
+
+
+NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
+
+
+def cfd_filter_noalloc(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=None, stream=None):
+    """cfd_filter for callers that may not allocate device memory: the library's
+    static 64 MiB device scratch replaces the workspace.  `moments`, if given,
+    is a caller-owned float64 device tensor [n_s, 2 n_p]; nothing is allocated
+    here.  Calls must not overlap on the GPU (they share the scratch)."""
+    blk = block_of(X)
+    _check(lib().cfd_filter_noalloc(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(moments),
+                                    _stream(stream)))
+
