@@ -27,6 +27,16 @@ UNIT = "GB/s"
 WORKLOAD = workloads.MEDIUM
 BOUNDS = (-8.6, 8.6)          # contains the Gershgorin interval [-8.5, 8.5] of the gamma = 1 lattice
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_hbm_gbs():
+    """Measured HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return HBM_FALLBACK_GBS, "fallback"
 
 
 def parse():
@@ -39,6 +49,8 @@ def parse():
     ap.add_argument("--n-p", type=int, default=WORKLOAD.n_p)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg (profiling runs)")
+    ap.add_argument("--prec", default="c128", choices=["c128", "c64"], help="filter arithmetic")
     return ap.parse_args()
 
 
@@ -119,7 +131,7 @@ def run_reference(a):
     if rank != 0:
         return
     w = WORKLOAD
-    steps = a.cpu_sample_steps or 40
+    steps = a.cpu_sample_steps or 150
     vals = []
     for _ in range(a.warmup if a.warmup < 1 else 1):
         cpu_oracle_sample(w, a.n_b, 2, w.seed)
@@ -157,13 +169,15 @@ def run_gpu(a):
     w = WORKLOAD
     n_b, n_p, n_s = a.n_b, a.n_p, w.n_s
     seed = w.seed + rank
+    prec = a.prec
+    cdt = torch.complex128 if prec == "c128" else torch.complex64
     H = b.cfd_build_matrix(b.topi_params(*w.lattice, t=w.t, m=w.m, gamma=w.gamma, seed=seed,
-                                         periodic=w.periodic), w.sell_C, w.sell_sigma, "c128")
+                                         periodic=w.periodic), w.sell_C, w.sell_sigma, prec)
     N, nnz = H.N, H.nnz
     lam_l, lam_r = -0.3, 0.3
-    X0 = torch.from_numpy(inputs.gaussian_block(N, n_s, seed=w.x_seed)).cuda()
+    X0 = torch.from_numpy(inputs.gaussian_block(N, n_s, seed=w.x_seed)).to(cdt).cuda()
     X = X0.clone()
-    ws = b.cfd_filter_workspace(N, n_s, n_b, n_p, "c128", "c128")
+    ws = b.cfd_filter_workspace(N, n_s, n_b, n_p, prec, prec)
     work = torch.empty(ws, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -193,7 +207,7 @@ def run_gpu(a):
     clocks = clk.summary()
 
     n_blocks = n_s // n_b
-    step_bytes = model.step_bytes(N, nnz, n_b, "c128")
+    step_bytes = model.step_bytes(N, nnz, n_b, prec)
     filt_bytes = n_blocks * n_p * step_bytes
     filt_flops = n_blocks * n_p * model.step_flops(N, nnz, n_b)
     value = world * a.steps * filt_bytes / t / 1e9
@@ -225,28 +239,38 @@ def run_gpu(a):
             tt = torch.tensor([te], device="cuda", dtype=torch.float64)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             te = float(tt.item())
-        nbytes = N * n_s * 16
+        nbytes = N * n_s * (16 if prec == "c128" else 8)
         e2e = {"value": round(world * a.steps * filt_bytes / te / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    hbm, hbm_src = measured_hbm_gbs()
+    gbs_launch = step_bytes / t_launch / 1e9
+    if prec == "c128":
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GFLOPS, 1),
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "peak_source": "nominal FP64 FMA rate (152 SMs x 2/clk x 2.07 GHz)",
+                "kernel": "k_cheb_step<double,%d,%d,GENERAL>" % (n_b, 1 if n_b <= 32 else 2),
+                "avg_launch_ms": round(1e3 * t_launch, 4),
+                "hbm_gbs": round(gbs_launch, 1), "hbm_frac": round(gbs_launch / hbm, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs_launch, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(gbs_launch / hbm, 4), "traffic": None, "peak_source": hbm_src,
+                "kernel": "k_cheb_step<float,%d,2,GENERAL>" % n_b, "avg_launch_ms": round(1e3 * t_launch, 4)}
     if rank == 0:
         cpu = None
-        if world == 1:
-            v, dt, cores, sst = cpu_oracle_sample(w, n_b, a.cpu_sample_steps or 40, seed)
+        if world == 1 and not a.no_cpu:
+            v, dt, cores, sst = cpu_oracle_sample(w, n_b, a.cpu_sample_steps or 150, seed)
             cpu = {"value": round(v, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "%d fused steps of one n_b=%d block of %s, fp64 C oracle, %.1f s" % (sst, n_b, w.name, dt)}
         out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": round(1e3 * t / a.steps, 3), "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+               "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
                "config": {"workload": w.name, "lattice": list(w.lattice), "N": N, "nnz": nnz, "n_s": n_s,
                           "n_b": n_b, "n_p": n_p, "sell_C": w.sell_C, "sell_sigma": w.sell_sigma,
                           "l2": "inputs larger than L2 (X 1.07 GB, work blocks 0.54 GB)",
                           "parallelism": "replicas" if world > 1 else "single"},
                "gflops": round(gflops, 2),
-               "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GFLOPS, 1),
-                            "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
-                            "kernel": "k_cheb_step<double,32,1,GENERAL>", "avg_launch_ms": round(1e3 * t_launch, 4),
-                            "hbm_frac_of_measured": round(step_bytes / t_launch / 1e9 / 6787.2, 4)},
+               "roofline": roof,
                "clocks": clocks, "gpu_launches": a.steps * launches_per_step,
                "cpu_baseline": cpu, "e2e": e2e}
         print(json.dumps(out))
