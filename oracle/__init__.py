@@ -323,9 +323,9 @@ def solve(H, lmin, lmax, lam_l, lam_r, n_p, X0, n_b, tol=1e-10, max_iter=50, n_t
     """ChebFD restart loop (Sect. 2): filter, orthogonalise, Rayleigh-Ritz.
     The paper gives no stopping rule; reading: a Ritz pair inside
     [lam_l, lam_r] is converged when its residual is <= tol; the loop stops
-    when the number of converged in-window pairs reaches n_t (n_t > 0), or,
-    with n_t = 0, when that number is >= 1 and unchanged over three
-    consecutive iterations.  In-window Ritz values inside a spectral gap
+    when the number of converged in-window pairs reaches n_t (n_t > 0), or
+    when that number is >= 1 and unchanged over three consecutive iterations
+    (a window holding fewer than n_t states still terminates).  In-window Ritz values inside a spectral gap
     (mixtures of states from both sides of the window) never converge and are
     not counted.  Returns (theta, r, X, iterations, converged) with theta, r
     the converged in-window pairs."""
@@ -338,7 +338,7 @@ def solve(H, lmin, lmax, lam_l, lam_r, n_p, X0, n_b, tol=1e-10, max_iter=50, n_t
         th, X, r = rayleigh_ritz(H, X)
         conv = (th >= lam_l) & (th <= lam_r) & (r <= tol)
         hist.append(int(conv.sum()))
-        done = (hist[-1] >= n_t) if n_t > 0 else (
+        done = (n_t > 0 and hist[-1] >= n_t) or (
             len(hist) >= 3 and hist[-1] >= 1 and hist[-1] == hist[-2] == hist[-3])
         if done:
             return th[conv], r[conv], X, it, True
