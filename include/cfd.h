@@ -253,6 +253,139 @@ cfd_status cfd_filter_noalloc(const cfd_matrix *H, double lmin, double lmax, dou
                               double lam_r, int n_p, cfd_block X, int n_b, double *moments,
                               cudaStream_t stream);
 
+
+/* ------------------------------------------------------------------------ */
+/* Spectral bounds                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Device scratch bytes cfd_spectral_bounds needs. */
+size_t cfd_spectral_bounds_workspace(int64_t N, int steps);
+
+/*
+ * Interval [lmin, lmax] containing the spectrum of H, for the affine map of
+ * the filter (Algorithm 1 maps the spectrum into [-1, 1]; the paper does not
+ * say how the bounds are found).  Reading: `steps` Lanczos steps (no
+ * reorthogonalisation) from a Gaussian start vector drawn from SplitMix64
+ * (seed, stream tag 2); the extreme Ritz values theta_1, theta_m are widened
+ * by their residual bounds |beta_m y_{m,i}| plus 1% of theta_m - theta_1 and
+ * clipped to the Gershgorin interval.  H must be CFD_C128; steps in 2..256.
+ * Host outputs: synchronises `stream`.
+ */
+cfd_status cfd_spectral_bounds(const cfd_matrix *H, int steps, uint64_t seed, double *lmin, double *lmax,
+                               void *work, size_t work_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Dense fp64 kernels: Gram, Hermitian eigensolver                           */
+/* ------------------------------------------------------------------------ */
+
+/* Device scratch bytes of cfd_block_gram for N rows, n_x and n_y columns. */
+size_t cfd_gram_workspace(int64_t N, int n_x, int n_y);
+
+/*
+ * S = X^H Y (n_x x n_y complex double, row-major, ld lds, device) for two
+ * CFD_C128 blocks with the same rows, on the FP64 tensor cores, reduced in a
+ * fixed order (deterministic).  n_x, n_y <= 256.  Asynchronous.
+ */
+cfd_status cfd_block_gram(cfd_block X, cfd_block Y, void *S, int64_t lds, void *work, size_t work_bytes,
+                          cudaStream_t stream);
+
+/* Device scratch bytes of cfd_eigh for order n. */
+size_t cfd_eigh_workspace(int n);
+
+/*
+ * Eigen-decomposition of the Hermitian part of the n x n complex double
+ * matrix A (row-major, ld lda, device; n <= 256) by cyclic Jacobi with
+ * round-robin parallel ordering: evals (device, n doubles) ascending, Q
+ * (device, ld ldq) with the eigenvectors as columns.  Sweeps stop when the
+ * off-diagonal Frobenius norm is below n * 2^-52 times the Frobenius norm.
+ * Asynchronous.
+ */
+cfd_status cfd_eigh(const void *A, int64_t lda, int n, double *evals, void *Q, int64_t ldq, void *work,
+                    size_t work_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Orthogonalisation and Rayleigh-Ritz (restart step of Sect. 2)             */
+/* ------------------------------------------------------------------------ */
+
+/* Device scratch bytes of cfd_orthogonalize for an N x n_s block. */
+size_t cfd_orthogonalize_workspace(int64_t N, int n_s);
+
+/*
+ * Orthonormalise the columns of X (CFD_C128, n_s <= 256) in place with SVQB
+ * (Stathopoulos & Wu 2002, the rank-revealing method Sect. 2 names): S = X^H X,
+ * D = diag(S)^{-1/2}, D S D = Q Theta Q^H, X <- X D Q Theta^{-1/2}, where
+ * Theta is clamped below at tol * max(Theta) (tol <= 0: 1e-14); applied twice.
+ * rank (host, nullable) receives #{theta >= tol max theta} of the first pass
+ * and then the call synchronises `stream`; otherwise it is asynchronous.
+ */
+cfd_status cfd_orthogonalize(cfd_block X, double tol, int *rank, void *work, size_t work_bytes,
+                             cudaStream_t stream);
+
+/* Device scratch bytes of cfd_rayleigh_ritz for an N x n_s block. */
+size_t cfd_rayleigh_ritz_workspace(int64_t N, int n_s);
+
+/*
+ * Rayleigh-Ritz on the orthonormal block X (CFD_C128) with the complex-double
+ * matrix H: Z = H X, G = X^H Z, G = Y diag(theta) Y^H (Jacobi), X <- X Y, and
+ * resid[j] = ||H x_j - theta_j x_j||_2.  evals (device, n_s, ascending) and
+ * resid (device, nullable).  Asynchronous.
+ */
+cfd_status cfd_rayleigh_ritz(const cfd_matrix *H, cfd_block X, double *evals, double *resid, void *work,
+                             size_t work_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* The ChebFD solve                                                          */
+/* ------------------------------------------------------------------------ */
+
+typedef enum cfd_policy {
+    CFD_POLICY_FP64 = 0,   /* every filter application in fp64 */
+    CFD_POLICY_MIXED = 1   /* fp32 filter until it stalls, then fp64; SVQB and RR always fp64 */
+} cfd_policy;
+
+typedef struct cfd_solve_params {
+    double lam_l, lam_r;   /* search interval */
+    double lmin, lmax;     /* spectral bounds; lmin >= lmax: found by cfd_spectral_bounds */
+    double tol;            /* residual tolerance ||H x - theta x||_2, unit vectors (e.g. 1e-10) */
+    double switch_tol;     /* mixed: fp32 phase target residual (<= 0: 1e-4) */
+    uint64_t seed;         /* start block (stream tag 1) and Lanczos (tag 2) */
+    int32_t n_s, n_p, n_b; /* search vectors, filter degree, subspace block */
+    int32_t n_t;           /* target eigenpair count (0: unknown) */
+    int32_t max_iter;
+    int32_t policy;        /* cfd_policy */
+    int32_t bounds_steps;  /* Lanczos steps (<= 0: 40) */
+    int32_t start;         /* 0: random start block; 1: X holds the start block */
+} cfd_solve_params;
+
+typedef struct cfd_solve_result {
+    int32_t n_conv;        /* converged Ritz pairs inside the window */
+    int32_t iters;         /* restart iterations */
+    int32_t iters_low;     /* of which with the fp32 filter */
+    int32_t rank_min;      /* smallest SVQB rank seen */
+    double lmin, lmax;     /* spectral bounds used */
+    double t_filter, t_orth, t_rr, t_total;   /* seconds (device events; t_total wall clock) */
+} cfd_solve_result;
+
+/* Device scratch bytes of cfd_solve. */
+size_t cfd_solve_workspace(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_solve_params *p);
+
+/*
+ * Chebyshev filter diagonalization (Sect. 2): repeat { filter X (Algorithms 1
+ * and 2), SVQB-orthogonalise, Rayleigh-Ritz } until done.  The paper gives no
+ * stopping rule; reading: a Ritz pair inside [lam_l, lam_r] is converged when
+ * its residual <= tol; stop when the converged count reaches n_t (n_t > 0), or
+ * when it is >= 1 and unchanged over three consecutive iterations.
+ * Mixed policy: the filter runs on H_low (CFD_C64 copy of H) with fp32
+ * arithmetic until the in-window count at switch_tol reaches n_t or stops
+ * growing, then on H in fp64; SVQB, Rayleigh-Ritz and residuals stay fp64.
+ * H: CFD_C128.  X: N x n_s CFD_C128, in: start block if p->start, out: Ritz
+ * vectors.  evals/resid: host arrays of n_s (all Ritz values, ascending, and
+ * their residuals).  Synchronises `stream` once per iteration.
+ * Errors: CFD_ERR_ARG, CFD_ERR_OOM, CFD_ERR_NOCONV (results still filled).
+ */
+cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_solve_params *p, cfd_block X,
+                     double *evals, double *resid, void *work, size_t work_bytes, cfd_solve_result *res,
+                     cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,23 @@ class cfd_block(ctypes.Structure):
                 ("n_cols", ctypes.c_int32), ("prec", ctypes.c_int32)]
 
 
+class cfd_solve_params(ctypes.Structure):
+    _fields_ = [("lam_l", ctypes.c_double), ("lam_r", ctypes.c_double), ("lmin", ctypes.c_double),
+                ("lmax", ctypes.c_double), ("tol", ctypes.c_double), ("switch_tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("n_s", ctypes.c_int32), ("n_p", ctypes.c_int32),
+                ("n_b", ctypes.c_int32), ("n_t", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("policy", ctypes.c_int32), ("bounds_steps", ctypes.c_int32), ("start", ctypes.c_int32)]
+
+
+class cfd_solve_result(ctypes.Structure):
+    _fields_ = [("n_conv", ctypes.c_int32), ("iters", ctypes.c_int32), ("iters_low", ctypes.c_int32),
+                ("rank_min", ctypes.c_int32), ("lmin", ctypes.c_double), ("lmax", ctypes.c_double),
+                ("t_filter", ctypes.c_double), ("t_orth", ctypes.c_double), ("t_rr", ctypes.c_double),
+                ("t_total", ctypes.c_double)]
+
+
+CFD_POLICY_FP64, CFD_POLICY_MIXED = 0, 1
+
 # ---------------------------------------------------------------- load --
 
 _LIB = None
@@ -84,6 +101,28 @@ _PROTOS = {
     "cfd_filter": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "cfd_spectral_bounds_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int]),
+    "cfd_spectral_bounds": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_int, ctypes.c_uint64,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "cfd_gram_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
+    "cfd_block_gram": (ctypes.c_int, [cfd_block, cfd_block, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_size_t, ctypes.c_void_p]),
+    "cfd_eigh_workspace": (ctypes.c_size_t, [ctypes.c_int]),
+    "cfd_eigh": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "cfd_orthogonalize_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int]),
+    "cfd_orthogonalize": (ctypes.c_int, [cfd_block, ctypes.c_double, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                         ctypes.c_size_t, ctypes.c_void_p]),
+    "cfd_rayleigh_ritz_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int]),
+    "cfd_rayleigh_ritz": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), cfd_block, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "cfd_solve_workspace": (ctypes.c_size_t, [ctypes.POINTER(cfd_matrix), ctypes.POINTER(cfd_matrix),
+                                              ctypes.POINTER(cfd_solve_params)]),
+    "cfd_solve": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.POINTER(cfd_matrix),
+                                 ctypes.POINTER(cfd_solve_params), cfd_block, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(cfd_solve_result),
+                                 ctypes.c_void_p]),
     "cfd_filter_noalloc": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block,
                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
@@ -236,6 +275,87 @@ def cfd_filter(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=Non
     _check(lib().cfd_filter(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
                             _ptr(mu), _stream(stream)))
     return mu
+
+
+# ------------------------------------------------------- bounds, dense --
+
+def cfd_spectral_bounds(H, steps=40, seed=3, stream=None):
+    """(lmin, lmax) enclosing the spectrum of the complex-double matrix H."""
+    ws = lib().cfd_spectral_bounds_workspace(H.N, steps)
+    work = _workspace(ws, H.buffers["val"].device)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib().cfd_spectral_bounds(H.ref(), steps, seed, ctypes.byref(lo), ctypes.byref(hi), _ptr(work), ws,
+                                     _stream(stream)))
+    return lo.value, hi.value
+
+
+def cfd_block_gram(X, Y, stream=None):
+    """S = X^H Y (complex double device tensor)."""
+    bx, by = block_of(X), block_of(Y)
+    S = torch.empty(bx.n_cols, by.n_cols, dtype=torch.complex128, device=X.device)
+    ws = lib().cfd_gram_workspace(bx.n_rows, bx.n_cols, by.n_cols)
+    work = _workspace(ws, X.device)
+    _check(lib().cfd_block_gram(bx, by, _ptr(S), S.stride(0), _ptr(work), ws, _stream(stream)))
+    return S
+
+
+def cfd_eigh(A, stream=None):
+    """(evals ascending, Q) of the Hermitian part of a complex double device matrix."""
+    n = A.shape[0]
+    ev = torch.empty(n, dtype=torch.float64, device=A.device)
+    Q = torch.empty(n, n, dtype=torch.complex128, device=A.device)
+    ws = lib().cfd_eigh_workspace(n)
+    work = _workspace(ws, A.device)
+    _check(lib().cfd_eigh(_ptr(A), A.stride(0), n, _ptr(ev), _ptr(Q), Q.stride(0), _ptr(work), ws,
+                          _stream(stream)))
+    return ev, Q
+
+
+def cfd_orthogonalize(X, tol=0.0, stream=None):
+    """SVQB-orthonormalise the columns of X in place; returns the rank of the first pass."""
+    blk = block_of(X)
+    ws = lib().cfd_orthogonalize_workspace(blk.n_rows, blk.n_cols)
+    work = _workspace(ws, X.device)
+    rank = ctypes.c_int()
+    _check(lib().cfd_orthogonalize(blk, tol, ctypes.byref(rank), _ptr(work), ws, _stream(stream)))
+    return rank.value
+
+
+def cfd_rayleigh_ritz(H, X, stream=None):
+    """Rayleigh-Ritz in place on X; returns (theta, residual norms) as device tensors."""
+    blk = block_of(X)
+    ev = torch.empty(blk.n_cols, dtype=torch.float64, device=X.device)
+    rs = torch.empty(blk.n_cols, dtype=torch.float64, device=X.device)
+    ws = lib().cfd_rayleigh_ritz_workspace(blk.n_rows, blk.n_cols)
+    work = _workspace(ws, X.device)
+    _check(lib().cfd_rayleigh_ritz(H.ref(), blk, _ptr(ev), _ptr(rs), _ptr(work), ws, _stream(stream)))
+    return ev, rs
+
+
+def cfd_solve(H, X, lam_l, lam_r, n_p, n_b, H_low=None, policy=CFD_POLICY_FP64, lmin=0.0, lmax=0.0,
+              tol=1e-10, n_t=0, max_iter=50, seed=2, start=0, switch_tol=0.0, bounds_steps=40, work=None,
+              stream=None, raise_noconv=True):
+    """Run the ChebFD solve on the N x n_s complex double tensor X (in: start block
+    when start=1; out: Ritz vectors).  Returns (evals, resid, cfd_solve_result)
+    with host numpy arrays of all n_s Ritz values and residuals."""
+    import numpy as np
+    blk = block_of(X)
+    p = cfd_solve_params(lam_l=lam_l, lam_r=lam_r, lmin=lmin, lmax=lmax, tol=tol, switch_tol=switch_tol,
+                         seed=seed, n_s=blk.n_cols, n_p=n_p, n_b=n_b, n_t=n_t, max_iter=max_iter, policy=policy,
+                         bounds_steps=bounds_steps, start=start)
+    hl = H_low.ref() if H_low is not None else None
+    ws = lib().cfd_solve_workspace(H.ref(), hl, ctypes.byref(p))
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, X.device)
+    ev = np.zeros(blk.n_cols)
+    rs = np.zeros(blk.n_cols)
+    res = cfd_solve_result()
+    st = lib().cfd_solve(H.ref(), hl, ctypes.byref(p), blk, ev.ctypes.data_as(ctypes.c_void_p),
+                         rs.ctypes.data_as(ctypes.c_void_p), _ptr(work), work.numel(), ctypes.byref(res),
+                         _stream(stream))
+    if st != 0 and (raise_noconv or st != 6):
+        _check(st)
+    return ev, rs, res
 
 
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024

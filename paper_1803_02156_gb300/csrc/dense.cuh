@@ -1,0 +1,36 @@
+// Dense fp64 building blocks for orthogonalisation and Rayleigh-Ritz.
+#pragma once
+
+#include "common.cuh"
+
+namespace cfd {
+
+constexpr int GRAM_MAX_SPLITS = 256;   // K-splits of a Gram (partials in the workspace)
+constexpr int GRAM_TARGET_CTAS = 640;  // CTAs per Gram launch (about 4 per SM)
+constexpr int RESID_MAX_CTAS = 1024;
+constexpr int DENSE_MAX_COLS = 256;     // widest block for Gram / projection / Jacobi
+
+// S (na x nb complex, ld lds) = X^H Y for N x na and N x nb blocks (unit column
+// stride, ld in complex elements).  Deterministic (fixed-order split reduction).
+size_t gram_workspace(int64_t K, int na, int nb);
+cfd_status gram(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nb, int64_t K,
+                double2 *S, int64_t lds, double *work, cudaStream_t stream);
+
+// X[:, 0:n_out] <- X[:, 0:n_in] M (M n_in x n_out complex, ld ldm), in place, n_out <= n_in.
+size_t project_workspace(int n_in, int n_out);
+cfd_status project_inplace(double2 *X, int64_t ldx, int64_t n_rows, int n_in, const double2 *M, int64_t ldm,
+                           int n_out, double *work, cudaStream_t stream);
+
+// Eigen-decomposition of the Hermitian part of A (n x n): eigenvalues ascending
+// in evals[n], eigenvectors in the columns of Q (ld ldq).  sweeps (host, nullable)
+// receives the Jacobi sweep count after the stream completes.
+size_t eigh_workspace(int n);
+cfd_status eigh(const double2 *A, int64_t lda, int n, double *evals, double2 *Q, int64_t ldq, void *work,
+                size_t work_bytes, cudaStream_t stream, int *sweeps);
+
+// out[j] = || Z_j - theta_j X_j ||_2 (theta, X nullable: column norms of Z).
+size_t resid_workspace(int n);
+cfd_status resid_norms(const double2 *Z, int64_t ldz, const double2 *X, int64_t ldx, const double *theta, int n,
+                       int64_t n_rows, double *out, double *work, cudaStream_t stream);
+
+}  // namespace cfd

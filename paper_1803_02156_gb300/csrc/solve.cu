@@ -1,0 +1,176 @@
+// The ChebFD restart loop (Sect. 2): filter, SVQB orthogonalisation,
+// Rayleigh-Ritz, convergence test; fp64 or mixed-precision filter policy.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "dense.cuh"
+#include "filter.cuh"
+
+namespace cfd {
+
+size_t orthogonalize_workspace(int64_t N, int n);
+cfd_status orthogonalize_impl(const cfd_block &X, double tol, int *rank_host, int *rank_dev, void *work,
+                              size_t work_bytes, cudaStream_t stream);
+size_t rr_workspace(int64_t N, int n);
+cfd_status rayleigh_ritz_impl(const cfd_matrix *H, const cfd_block &X, double *evals, double *resid, void *work,
+                              size_t work_bytes, cudaStream_t stream);
+size_t bounds_workspace(int64_t N, int steps);
+cfd_status spectral_bounds_dev(const cfd_matrix *H, int steps, uint64_t seed, double *out_dev, void *work,
+                               size_t work_bytes, cudaStream_t stream);
+cfd_status gaussian_block(double2 *X, int64_t ldx, int64_t N, int n, uint64_t seed, uint64_t tag, int col0,
+                          int n_total, cudaStream_t stream);
+
+namespace {
+
+struct SolveWs {
+    size_t filt, orth, rr, bnd, total;
+};
+
+SolveWs solve_ws(const cfd_matrix *H, const cfd_matrix *Hl, const cfd_solve_params *p) {
+    SolveWs w;
+    int64_t N = H->n_rows;
+    w.filt = filter_workspace(N, p->n_s, p->n_b, p->n_p, CFD_C128, CFD_C128);
+    if (Hl) w.filt = std::max(w.filt, filter_workspace(N, p->n_s, p->n_b, p->n_p, CFD_C64, CFD_C128));
+    w.orth = orthogonalize_workspace(N, p->n_s) + 256;
+    w.rr = rr_workspace(N, p->n_s);
+    w.bnd = bounds_workspace(N, std::max(2, p->bounds_steps > 0 ? p->bounds_steps : 40)) + 256;
+    // phases run one after another: the scratch is shared
+    w.total = round_up(std::max(std::max(w.filt, w.orth), std::max(w.rr, w.bnd)), 256) + 8192;
+    return w;
+}
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+}  // namespace cfd
+
+using namespace cfd;
+
+extern "C" {
+
+size_t cfd_solve_workspace(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_solve_params *p) {
+    if (!H || !p || p->n_s < 1 || p->n_b < 1 || p->n_p < 2) return 0;
+    return solve_ws(H, H_low, p).total;
+}
+
+cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_solve_params *p, cfd_block X,
+                     double *evals, double *resid, void *work, size_t work_bytes, cfd_solve_result *res,
+                     cudaStream_t stream) {
+    clear_error();
+    CFD_TRY(check_matrix(H));
+    if (!p || !evals || !resid || !res || !work) return fail(CFD_ERR_ARG, "NULL argument");
+    if (H->prec != CFD_C128) return fail(CFD_ERR_ARG, "cfd_solve needs the complex-double matrix as H");
+    const bool mixed = p->policy == CFD_POLICY_MIXED;
+    if (mixed) {
+        if (!H_low) return fail(CFD_ERR_ARG, "mixed policy needs the complex-float matrix H_low");
+        CFD_TRY(check_matrix(H_low));
+        if (H_low->prec != CFD_C64 || H_low->n_rows != H->n_rows)
+            return fail(CFD_ERR_ARG, "H_low must be the complex-float copy of H");
+    } else if (p->policy != CFD_POLICY_FP64) {
+        return fail(CFD_ERR_ARG, "unknown policy %d", p->policy);
+    }
+    if (X.prec != CFD_C128 || X.n_cols != p->n_s || X.n_rows != H->n_rows)
+        return fail(CFD_ERR_ARG, "X must be the N x n_s complex-double block");
+    if (!(p->lam_l < p->lam_r)) return fail(CFD_ERR_ARG, "empty search window");
+    if (p->max_iter < 1 || p->tol <= 0) return fail(CFD_ERR_ARG, "max_iter and tol must be positive");
+    SolveWs ws = solve_ws(H, mixed ? H_low : nullptr, p);
+    if (work_bytes < ws.total) return fail(CFD_ERR_OOM, "solve workspace %zu < %zu bytes", work_bytes, ws.total);
+
+    const double t0 = now_s();
+    char *scratch = static_cast<char *>(work) + 8192;      // first 8 KB: small device results
+    size_t scratch_bytes = work_bytes - 8192;
+    double *small = static_cast<double *>(work);           // [0..3] bounds
+    double2 *Xp = static_cast<double2 *>(X.ptr);
+    const int n = p->n_s;
+    std::memset(res, 0, sizeof(*res));
+
+    if (p->start == 0) CFD_TRY(gaussian_block(Xp, X.ld, X.n_rows, n, p->seed, 1, 0, n, stream));
+
+    double lmin = p->lmin, lmax = p->lmax;
+    if (!(lmin < lmax)) {
+        int steps = p->bounds_steps > 0 ? p->bounds_steps : 40;
+        CFD_TRY(spectral_bounds_dev(H, steps, p->seed, small, scratch, scratch_bytes, stream));
+        double h[2];
+        CFD_CUDA(cudaMemcpyAsync(h, small, sizeof(h), cudaMemcpyDeviceToHost, stream));
+        CFD_CUDA(cudaStreamSynchronize(stream));
+        lmin = h[0];
+        lmax = h[1];
+    }
+    res->lmin = lmin;
+    res->lmax = lmax;
+    if (!(lmin <= p->lam_l && p->lam_r <= lmax))
+        return fail(CFD_ERR_ARG, "window [%g, %g] not inside the spectral bounds [%g, %g]", p->lam_l, p->lam_r,
+                    lmin, lmax);
+
+    double *ev_dev = reinterpret_cast<double *>(static_cast<char *>(work) + 1024);   // n <= 256 doubles
+    double *rs_dev = ev_dev + DENSE_MAX_COLS;
+    std::vector<int> hist, hist_low;
+    bool low = mixed;
+    const double switch_tol = p->switch_tol > 0 ? p->switch_tol : 1e-4;
+    res->rank_min = n;
+    for (int it = 1; it <= p->max_iter; ++it) {
+        cudaEvent_t e0, e1, e2, e3;
+        cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); cudaEventCreate(&e3);
+        cudaEventRecord(e0, stream);
+        CFD_TRY(filter_impl(low ? H_low : H, lmin, lmax, p->lam_l, p->lam_r, p->n_p, X, p->n_b, 0, 0, scratch,
+                            scratch_bytes, nullptr, stream));
+        cudaEventRecord(e1, stream);
+        int rank = n;
+        CFD_TRY(orthogonalize_impl(X, 1e-14, nullptr, reinterpret_cast<int *>(small + 8), scratch, scratch_bytes,
+                                   stream));
+        cudaEventRecord(e2, stream);
+        CFD_TRY(rayleigh_ritz_impl(H, X, ev_dev, rs_dev, scratch, scratch_bytes, stream));
+        cudaEventRecord(e3, stream);
+        CFD_CUDA(cudaMemcpyAsync(evals, ev_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));
+        CFD_CUDA(cudaMemcpyAsync(resid, rs_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));
+        CFD_CUDA(cudaMemcpyAsync(&rank, small + 8, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CFD_CUDA(cudaStreamSynchronize(stream));
+        float a = 0, b = 0, c = 0;
+        cudaEventElapsedTime(&a, e0, e1);
+        cudaEventElapsedTime(&b, e1, e2);
+        cudaEventElapsedTime(&c, e2, e3);
+        cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); cudaEventDestroy(e3);
+        res->t_filter += a * 1e-3;
+        res->t_orth += b * 1e-3;
+        res->t_rr += c * 1e-3;
+        res->rank_min = std::min(res->rank_min, rank);
+        res->iters = it;
+        if (low) res->iters_low = it;
+
+        int cnt = 0, cnt_low = 0;
+        for (int j = 0; j < n; ++j) {
+            bool in = evals[j] >= p->lam_l && evals[j] <= p->lam_r;
+            if (in && resid[j] <= p->tol) ++cnt;
+            if (in && resid[j] <= switch_tol) ++cnt_low;
+        }
+        res->n_conv = cnt;
+        hist.push_back(cnt);
+        if (!low) {
+            size_t h = hist.size();
+            bool done = (p->n_t > 0 && cnt >= p->n_t) ||
+                        (h >= 3 && cnt >= 1 && hist[h - 1] == hist[h - 2] && hist[h - 2] == hist[h - 3]);
+            if (done) {
+                res->t_total = now_s() - t0;
+                return CFD_OK;
+            }
+        } else {
+            // switch to the fp64 filter once the fp32 filter has delivered the target
+            // count to switch_tol, or that count stopped growing
+            hist_low.push_back(cnt_low);
+            size_t h = hist_low.size();
+            if ((p->n_t > 0 && cnt_low >= p->n_t) || (h >= 2 && cnt_low >= 1 && hist_low[h - 1] <= hist_low[h - 2])) {
+                low = false;
+                hist.clear();
+            }
+        }
+    }
+    res->t_total = now_s() - t0;
+    return fail(CFD_ERR_NOCONV, "no convergence in %d iterations (%d converged)", p->max_iter, res->n_conv);
+}
+
+}  // extern "C"
