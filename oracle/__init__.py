@@ -325,22 +325,26 @@ def solve(H, lmin, lmax, lam_l, lam_r, n_p, X0, n_b, tol=1e-10, max_iter=50, n_t
     [lam_l, lam_r] is converged when its residual is <= tol; the loop stops
     when the number of converged in-window pairs reaches n_t (n_t > 0), or
     when that number is >= 1 and unchanged over three consecutive iterations
-    (a window holding fewer than n_t states still terminates).  In-window Ritz values inside a spectral gap
-    (mixtures of states from both sides of the window) never converge and are
-    not counted.  Returns (theta, r, X, iterations, converged) with theta, r
-    the converged in-window pairs."""
+    while the smallest residual of the unconverged in-window pairs did not
+    halve in either of the last two (no pair is still converging).  In-window
+    Ritz values inside a spectral gap (mixtures of states from both sides of
+    the window) never converge and are not counted.  Returns (theta, r, X,
+    iterations, converged) with theta, r the converged in-window pairs."""
     X = np.array(X0, dtype=np.complex128, copy=True)
-    hist = []
+    hist, mres = [], []
     th = r = None
     for it in range(1, max_iter + 1):
         X, _ = chebfd_filter(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b)
         X = mgs2(X)
         th, X, r = rayleigh_ritz(H, X)
-        conv = (th >= lam_l) & (th <= lam_r) & (r <= tol)
+        inside = (th >= lam_l) & (th <= lam_r)
+        conv = inside & (r <= tol)
         hist.append(int(conv.sum()))
-        done = (n_t > 0 and hist[-1] >= n_t) or (
-            len(hist) >= 3 and hist[-1] >= 1 and hist[-1] == hist[-2] == hist[-3])
-        if done:
+        rest = r[inside & ~conv]
+        mres.append(float(rest.min()) if rest.size else 1e300)      # none left: nothing improves
+        stable = (len(hist) >= 3 and hist[-1] >= 1 and hist[-1] == hist[-2] == hist[-3]
+                  and mres[-1] > 0.5 * mres[-2] and mres[-2] > 0.5 * mres[-3])
+        if (n_t > 0 and hist[-1] >= n_t) or stable:
             return th[conv], r[conv], X, it, True
     conv = (th >= lam_l) & (th <= lam_r) & (r <= tol)
     return th[conv], r[conv], X, max_iter, False
@@ -358,3 +362,19 @@ def window_from_dense(evals, target):
             if best is None or abs(k - target) < abs(best - target):
                 best = k
     return 0.5 * (a[best - 1] + a[best]), best
+
+
+def kpm_count(mu, N, lmin, lmax, lam_l, lam_r):
+    """Kernel-polynomial estimate of the number of eigenvalues in [lam_l, lam_r]
+    (Sect. 2: the Chebyshev moments monitor the number of states in the search
+    interval): the trace of the Jackson-damped window function, estimated with
+    the random vectors whose moments are the rows of mu,
+    count = N / R sum_r (sum_m g_m c_m mu_m(r)) / mu_0(r), with g_m the Jackson
+    kernel for M = n_mom moments and c_m the window coefficients."""
+    mu = np.atleast_2d(np.asarray(mu, dtype=np.float64))
+    n_mom = mu.shape[1]
+    c = window_coeffs(lam_l, lam_r, lmin, lmax, n_mom - 1)
+    g = jackson(n_mom - 1)
+    per = (mu @ (g * c)) / mu[:, 0]
+    return N * per.mean()
+

@@ -321,3 +321,49 @@ def test_traffic_model_reproduces_table3_and_eq2():
     for r in g["roofline_gflops"]:
         v = model.roofline(r["n_b"], r["bandwidth_gbs"])
         assert abs(v - r["value"]) / r["value"] < 0.01, (r, v)
+
+
+# ------------------------------------------------------------ KPM counting --
+
+def test_kpm_count_exact_with_full_basis():
+    """With the full standard basis as 'random' vectors the trace estimate is
+    exact for the damped window: sum_i p(lambda_i) over the dense spectrum."""
+    H = oracle.topi_csr(4, 4, 3, seed=8)
+    Hd = H.dense()
+    lam = np.linalg.eigvalsh(Hd)
+    E = np.eye(H.N, dtype=np.complex128)
+    n_p = 60
+    _, dots = oracle.chebfd_filter(H, -8.6, 8.6, -1.0, 1.0, n_p, E, 16)
+    mu = oracle.kpm_moments(dots)
+    cnt = oracle.kpm_count(mu, H.N, -8.6, 8.6, -0.8, 0.9)
+    a, b = oracle.spectral_map(-8.6, 8.6)
+    gc = oracle.jackson(2 * n_p - 1) * oracle.window_coeffs(-0.8, 0.9, -8.6, 8.6, 2 * n_p - 1)
+    ref = oracle.filter_polynomial(a * lam + b, gc).sum()
+    assert abs(cnt - ref) < 1e-9 * H.N
+
+
+def test_kpm_count_estimates_dense_count():
+    H = oracle.topi_csr(8, 8, 8, seed=1)
+    ev = np.linalg.eigvalsh(H.dense())
+    X = inputs.gaussian_block(H.N, 64, seed=21)
+    _, dots = oracle.chebfd_filter(H, -8.6, 8.6, -0.7, 0.7, 400, X, 32)
+    mu = oracle.kpm_moments(dots)
+    cnt = oracle.kpm_count(mu, H.N, -8.6, 8.6, -2.0, 2.0)
+    true = np.sum(np.abs(ev) <= 2.0)
+    assert abs(cnt - true) < 0.1 * true
+
+
+def test_library_kpm_functions_match_oracle():
+    """The library's host KPM count equals the oracle's on the same moments;
+    its window bisection hits the target count."""
+    from paper_1803_02156_gb300 import build, binding as b
+    build.build()
+    H = oracle.topi_csr(6, 6, 6, seed=2)
+    X = inputs.gaussian_block(H.N, 16, seed=4)
+    _, dots = oracle.chebfd_filter(H, -8.6, 8.6, -0.7, 0.7, 150, X, 16)
+    mu = oracle.kpm_moments(dots)
+    for win in [(-0.5, 0.5), (-3.0, 1.0), (2.0, 8.0)]:
+        assert abs(b.cfd_kpm_count(mu, H.N, -8.6, 8.6, *win) - oracle.kpm_count(mu, H.N, -8.6, 8.6, *win)) < 1e-9
+    lo, hi = b.cfd_kpm_window(mu, H.N, -8.6, 8.6, 0.0, 40.0)
+    assert abs(oracle.kpm_count(mu, H.N, -8.6, 8.6, lo, hi) - 40.0) < 1e-6
+    assert abs(lo + hi) < 1e-12
