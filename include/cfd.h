@@ -53,6 +53,26 @@ typedef enum cfd_prec {
     CFD_C64 = 1           /* complex float: fp32 arithmetic and accumulation */
 } cfd_prec;
 
+/*
+ * OR into the `prec` argument of the matrix queries/builds to store every
+ * nonzero as one real scalar instead of a complex pair: each row keeps its
+ * purely real entries first, then its purely imaginary entries (their
+ * imaginary parts), each group in ascending column order.  Valid for
+ * matrices whose every entry is purely real or purely imaginary, as all Topi
+ * entries are (on-site (m + V) Gamma_1 and hops +-t/2, +-i t/2).  A complex
+ * multiply-add with such an entry is two fused multiply-adds instead of four
+ * and the value is half the bytes; the row sums add the same products in
+ * another order (real group, then imaginary group), so results agree with
+ * the complex storage to rounding.
+ */
+#define CFD_PACK_RI 0x100
+
+/* cfd_matrix.flags bit: values are packed real-or-imaginary scalars. */
+#define CFD_MATRIX_PACKED 1
+/* cfd_matrix.flags bits 8..15: upper bound on the slots per row of any chunk
+ * (0: unknown). */
+#define CFD_MATRIX_SLOTS_SHIFT 8
+
 /* Human-readable name of a status code (static string). */
 const char *cfd_status_string(int status);
 
@@ -61,6 +81,10 @@ const char *cfd_last_error(void);
 
 /* Library version, e.g. "1.0.0" (static string). */
 const char *cfd_version(void);
+
+/* Number of GPU kernels this library has launched in this process (all
+ * threads and devices); for accounting in benchmarks. */
+unsigned long long cfd_launch_count(void);
 
 /* ------------------------------------------------------------------------ */
 /* Matrix: the topological-insulator Hamiltonian in SELL-C-sigma             */
@@ -112,12 +136,16 @@ typedef struct cfd_matrix_buffers {
  * sorted row r (r = c C + rr) sits at chunk_ptr[c] + k C + rr.  Within a row
  * the slots are in ascending column order; padding slots have col = -1 and
  * value 0.  Sorted row r is canonical row perm[r] (perm == NULL when
- * sigma == 1).  Column indices are canonical.  The struct only points into
- * caller memory.
+ * sigma == 1).  Column indices are canonical.  With CFD_MATRIX_PACKED, val
+ * holds one real scalar per slot (double or float); chunk_len[c] holds the
+ * chunk's real slot count in its low 16 bits and its imaginary slot count in
+ * the high 16 bits, slots [0, n_re) of a row hold real entries and
+ * [n_re, n_re + n_im) imaginary ones, each group padded separately (col -1,
+ * value 0).  The struct only points into caller memory.
  */
 typedef struct cfd_matrix {
     int64_t n_rows, nnz, n_chunks, n_slots;
-    int32_t C, sigma, prec, reserved;
+    int32_t C, sigma, prec, flags;    /* flags: CFD_MATRIX_PACKED, slot bound << CFD_MATRIX_SLOTS_SHIFT */
     void *val;
     int32_t *col;
     int64_t *chunk_ptr;
@@ -222,6 +250,109 @@ size_t cfd_filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, in
 cfd_status cfd_filter(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
                       int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
                       double *moments, cudaStream_t stream);
+
+/* Tuning knobs of the fused step kernels (zero = default). */
+typedef struct cfd_filter_opts {
+    int32_t vpt;          /* vectors per thread: 1 or 2 (threads per row = n_b / vpt); 1 needs n_b <= 32 */
+    int32_t grid_cap;     /* upper bound on CTAs per step launch (0: one wave of resident CTAs) */
+    int32_t persistent;   /* 1: all n_p steps of a block in one cooperative launch (no moments) */
+    int32_t staged;       /* 1: general steps stage matrix chunks in shared memory by TMA bulk copies;
+                             -1: never; 0: default (staged for complex-float matrices);
+                             2: test of the bounded waits (no wait can succeed; the filter
+                             records CFD_ERR_TIMEOUT, see cfd_workspace_status) */
+    int32_t reserved[4];
+} cfd_filter_opts;
+
+/* cfd_filter with explicit kernel options (the autotuner's knobs besides n_b,
+ * C and sigma).  The filtered block does not depend on the options; the
+ * moments only through the order of their reductions. */
+cfd_status cfd_filter_ex(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                         int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
+                         double *moments, const cfd_filter_opts *opts, cudaStream_t stream);
+
+/*
+ * Chebyshev moments only (the kernel polynomial method: Algorithm 1 without
+ * line 12, Sect. 2): for the columns of R (N x n_s, the matrix's precision,
+ * not modified) mu[j][m] = <r_j, T_m(H~) r_j>, m = 0..2 n_p - 1, into
+ * moments (device, [n_s][2 n_p]), with the same fused steps as cfd_filter but
+ * no accumulation into a filtered block (two fewer block vectors of traffic
+ * per step).  work: cfd_filter_workspace(N, n_s, n_b, n_p, prec, prec) bytes.
+ * Asynchronous.
+ */
+cfd_status cfd_kpm_moments(const cfd_matrix *H, double lmin, double lmax, int n_p, cfd_block R, int n_b,
+                           void *work, size_t work_bytes, double *moments, cudaStream_t stream);
+
+/*
+ * Estimated number of eigenvalues of H in [lam_l, lam_r] from Chebyshev
+ * moments (kernel polynomial method; Sect. 2 uses the moments to monitor the
+ * number of states in the search interval).  mu: host [n_vec][n_mom] moments
+ * <r, T_m(H~) r> of n_vec random vectors (e.g. cfd_filter's output with
+ * n_mom = 2 n_p); count = N / n_vec sum_r sum_m g_m c_m mu_m(r) / mu_0(r) with
+ * the Jackson kernel g_m for M = n_mom moments and the window coefficients
+ * c_m of cfd_filter_coeffs.  Host only.
+ */
+cfd_status cfd_kpm_count(const double *mu, int n_vec, int n_mom, int64_t N, double lmin, double lmax,
+                         double lam_l, double lam_r, double *count);
+
+/*
+ * Window [center - d, center + d] whose cfd_kpm_count equals `target`
+ * (bisection on d; the Jackson-damped count grows with d).  Host only.
+ * Errors: CFD_ERR_ARG if even the widest window holds fewer states.
+ */
+cfd_status cfd_kpm_window(const double *mu, int n_vec, int n_mom, int64_t N, double lmin, double lmax,
+                          double center, double target, double *lam_l, double *lam_r);
+
+/* ------------------------------------------------------------------------ */
+/* Batches of independent realisations                                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Sizes for a batch of R Topi realisations (p[0..R-1]: lattices and disorder
+ * seeds may all differ) stored as one block-diagonal SELL-C-sigma matrix.
+ * Realisation r owns rows [row_off[r], row_off[r + 1]): its 4 Nx Ny Nz rows
+ * followed by empty padding rows up to a multiple of max(C, sigma, 32), so no
+ * chunk or sorting window spans two realisations.  row_off (host, nullable)
+ * receives R + 1 offsets.  The chunk -> realisation map needs
+ * out->n_chunks int32 of device memory.  Host only.
+ */
+cfd_status cfd_batch_query_size(const cfd_topi_params *p, int R, int C, int sigma, int prec,
+                                cfd_matrix_sizes *out, int64_t *row_off);
+
+/*
+ * Build the batch into caller buffers (sizes from cfd_batch_query_size) and
+ * the chunk -> realisation map chunk_rid (device, n_chunks int32).  Each
+ * realisation's rows and values are exactly those of cfd_build_matrix for
+ * its parameters, shifted by row_off[r].  Asynchronous.
+ */
+cfd_status cfd_build_batch(const cfd_topi_params *p, int R, int C, int sigma, int prec,
+                           const cfd_matrix_buffers *buf, int32_t *chunk_rid, cfd_matrix *out,
+                           cudaStream_t stream);
+
+/* Device scratch bytes of cfd_filter_batched. */
+size_t cfd_filter_batched_workspace(int64_t N, int R, int n_s, int n_b, int n_p, int prec_H, int prec_X);
+
+/*
+ * The ChebFD filter on every realisation of a batch at once: each row uses
+ * the map alpha_r (H - beta_r) and the weights g_k c_k of its realisation r,
+ * from windows (device, [R][4] doubles: lmin, lmax, lam_l, lam_r).  X is the
+ * N_total x n_s block of all realisations (padding rows must be zero and stay
+ * zero).  With opts->persistent (default when opts is NULL) each n_b block is
+ * one cooperative launch running all n_p steps of all realisations, the grid
+ * synchronising between steps; otherwise one launch per step.  Per
+ * realisation the result equals cfd_filter on that realisation alone, bit for
+ * bit.  No moments.  Same precision rules as cfd_filter.  Asynchronous.
+ */
+cfd_status cfd_filter_batched(const cfd_matrix *H, const int32_t *chunk_rid, int R, const double *windows,
+                              int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
+                              const cfd_filter_opts *opts, cudaStream_t stream);
+
+/*
+ * Device-side status of a filter workspace (cfd_filter, cfd_filter_ex,
+ * cfd_filter_batched): the staged kernels bound every wait on their TMA
+ * copies and record CFD_ERR_TIMEOUT here if one expires.  Synchronises
+ * `stream`; returns CFD_OK or the recorded status.
+ */
+cfd_status cfd_workspace_status(const void *work, cudaStream_t stream);
 
 /* Size of the library-owned device scratch used by cfd_filter_noalloc. */
 #define CFD_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
@@ -373,10 +504,14 @@ size_t cfd_solve_workspace(const cfd_matrix *H, const cfd_matrix *H_low, const c
  * and 2), SVQB-orthogonalise, Rayleigh-Ritz } until done.  The paper gives no
  * stopping rule; reading: a Ritz pair inside [lam_l, lam_r] is converged when
  * its residual <= tol; stop when the converged count reaches n_t (n_t > 0), or
- * when it is >= 1 and unchanged over three consecutive iterations.
+ * when it is >= 1 and unchanged over three consecutive iterations while the
+ * smallest residual of the unconverged in-window pairs did not halve in
+ * either of the last two (no pair is still converging).
  * Mixed policy: the filter runs on H_low (CFD_C64 copy of H) with fp32
  * arithmetic until the in-window count at switch_tol reaches n_t or stops
- * growing, then on H in fp64; SVQB, Rayleigh-Ritz and residuals stay fp64.
+ * growing, then on H in fp64, where the solve also stops as soon as at least
+ * as many in-window pairs reach tol as the fp32 phase brought to switch_tol;
+ * SVQB, Rayleigh-Ritz and residuals stay fp64.
  * H: CFD_C128.  X: N x n_s CFD_C128, in: start block if p->start, out: Ritz
  * vectors.  evals/resid: host arrays of n_s (all Ritz values, ascending, and
  * their residuals).  Synchronises `stream` once per iteration.
@@ -385,6 +520,31 @@ size_t cfd_solve_workspace(const cfd_matrix *H, const cfd_matrix *H_low, const c
 cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_solve_params *p, cfd_block X,
                      double *evals, double *resid, void *work, size_t work_bytes, cfd_solve_result *res,
                      cudaStream_t stream);
+
+/* Device scratch bytes of cfd_solve_batched. */
+size_t cfd_solve_batched_workspace(const cfd_matrix *H, int R, const cfd_solve_params *p);
+
+/*
+ * The ChebFD solve (see cfd_solve) on every realisation of a batch at once.
+ * H (CFD_C128, optionally packed) and H_low (CFD_C64 copy, mixed policy only)
+ * come from cfd_build_batch with the chunk -> realisation map chunk_rid.
+ * Host arrays: row_off[R + 1] (cfd_batch_query_size), row_end[R] (end of
+ * each realisation's real rows, row_off[r] + 4 Nx Ny Nz), windows[R][4]
+ * (lmin, lmax, lam_l, lam_r per realisation), n_t[R] (target counts, 0 =
+ * unknown).  From p: n_s (<= 64), n_p, n_b, tol, max_iter, policy,
+ * switch_tol, seed, start.  X: N_total x n_s complex double with ld = n_s
+ * (padding rows are zeroed).  Each iteration is one batched filter (a
+ * persistent launch per n_b block for all realisations), a batched SVQB
+ * (twice) and a batched Rayleigh-Ritz.  Realisations stop counting once
+ * converged; the mixed policy switches to the fp64 filter when every
+ * realisation is ready.  Outputs (host): evals[R][n_s], resid[R][n_s],
+ * res[R].  Synchronises `stream` once per iteration.
+ */
+cfd_status cfd_solve_batched(const cfd_matrix *H, const cfd_matrix *H_low, const int32_t *chunk_rid, int R,
+                             const int64_t *row_off, const int64_t *row_end, const double *windows,
+                             const int32_t *n_t, const cfd_solve_params *p, cfd_block X, double *evals,
+                             double *resid, cfd_solve_result *res, void *work, size_t work_bytes,
+                             cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libcfd.so")
 
 CFD_C128, CFD_C64 = 0, 1
-PREC = {"c128": CFD_C128, "c64": CFD_C64}
+CFD_PACK_RI = 0x100
+# "p": values packed as real-or-imaginary scalars (CFD_PACK_RI)
+PREC = {"c128": CFD_C128, "c64": CFD_C64, "c128p": CFD_C128 | CFD_PACK_RI, "c64p": CFD_C64 | CFD_PACK_RI}
 TORCH_DTYPE = {CFD_C128: torch.complex128, CFD_C64: torch.complex64}
 SCALAR_BYTES = {CFD_C128: 16, CFD_C64: 8}
 
@@ -50,7 +52,7 @@ class cfd_matrix_buffers(ctypes.Structure):
 class cfd_matrix(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_chunks", ctypes.c_int64),
                 ("n_slots", ctypes.c_int64), ("C", ctypes.c_int32), ("sigma", ctypes.c_int32),
-                ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32), ("val", ctypes.c_void_p),
+                ("prec", ctypes.c_int32), ("flags", ctypes.c_int32), ("val", ctypes.c_void_p),
                 ("col", ctypes.c_void_p), ("chunk_ptr", ctypes.c_void_p),
                 ("chunk_len", ctypes.c_void_p), ("perm", ctypes.c_void_p)]
 
@@ -58,6 +60,11 @@ class cfd_matrix(ctypes.Structure):
 class cfd_block(ctypes.Structure):
     _fields_ = [("ptr", ctypes.c_void_p), ("n_rows", ctypes.c_int64), ("ld", ctypes.c_int64),
                 ("n_cols", ctypes.c_int32), ("prec", ctypes.c_int32)]
+
+
+class cfd_filter_opts(ctypes.Structure):
+    _fields_ = [("vpt", ctypes.c_int32), ("grid_cap", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("staged", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class cfd_solve_params(ctypes.Structure):
@@ -85,6 +92,7 @@ _PROTOS = {
     "cfd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cfd_last_error": (ctypes.c_char_p, []),
     "cfd_version": (ctypes.c_char_p, []),
+    "cfd_launch_count": (ctypes.c_ulonglong, []),
     "cfd_matrix_query_size": (ctypes.c_int, [ctypes.POINTER(cfd_topi_params), ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, ctypes.POINTER(cfd_matrix_sizes)]),
     "cfd_build_matrix": (ctypes.c_int, [ctypes.POINTER(cfd_topi_params), ctypes.c_int, ctypes.c_int,
@@ -101,6 +109,31 @@ _PROTOS = {
     "cfd_filter": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "cfd_filter_ex": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                     ctypes.POINTER(cfd_filter_opts), ctypes.c_void_p]),
+    "cfd_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "cfd_kpm_moments": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       cfd_block, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "cfd_kpm_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "cfd_kpm_window": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "cfd_batch_query_size": (ctypes.c_int, [ctypes.POINTER(cfd_topi_params), ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(cfd_matrix_sizes),
+                                            ctypes.c_void_p]),
+    "cfd_build_batch": (ctypes.c_int, [ctypes.POINTER(cfd_topi_params), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(cfd_matrix_buffers), ctypes.c_void_p,
+                                       ctypes.POINTER(cfd_matrix), ctypes.c_void_p]),
+    "cfd_filter_batched_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                       ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "cfd_filter_batched": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_int, cfd_block, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_size_t, ctypes.POINTER(cfd_filter_opts), ctypes.c_void_p]),
     "cfd_spectral_bounds_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int]),
     "cfd_spectral_bounds": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_int, ctypes.c_uint64,
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -123,6 +156,13 @@ _PROTOS = {
                                  ctypes.POINTER(cfd_solve_params), cfd_block, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(cfd_solve_result),
                                  ctypes.c_void_p]),
+    "cfd_solve_batched_workspace": (ctypes.c_size_t, [ctypes.POINTER(cfd_matrix), ctypes.c_int,
+                                                      ctypes.POINTER(cfd_solve_params)]),
+    "cfd_solve_batched": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.POINTER(cfd_matrix), ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.POINTER(cfd_solve_params), cfd_block,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(cfd_solve_result),
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "cfd_filter_noalloc": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block,
                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
@@ -175,6 +215,11 @@ def cfd_version():
     return lib().cfd_version().decode()
 
 
+def cfd_launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(lib().cfd_launch_count())
+
+
 # -------------------------------------------------------------- matrix --
 
 def topi_params(Nx, Ny, Nz, t=1.0, m=2.0, gamma=1.0, seed=1, periodic=(1, 1, 0)):
@@ -207,6 +252,10 @@ class Matrix:
     @property
     def prec(self):
         return self.c.prec
+
+    @property
+    def packed(self):
+        return bool(self.c.flags & 1)
 
     def ref(self):
         return ctypes.byref(self.c)
@@ -275,6 +324,105 @@ def cfd_filter(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=Non
     _check(lib().cfd_filter(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
                             _ptr(mu), _stream(stream)))
     return mu
+
+
+def cfd_filter_ex(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, vpt=0, grid_cap=0, moments=False, work=None,
+                  stream=None, persistent=0, staged=0):
+    """cfd_filter with the kernel options (vectors per thread, CTA cap, persistent
+    launch, TMA staging: 1 on, -1 off, 0 default)."""
+    blk = block_of(X)
+    ws = cfd_filter_workspace(H.N, blk.n_cols, n_b, n_p, H.prec, blk.prec)
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, X.device)
+    mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=X.device) if moments else None
+    o = cfd_filter_opts(vpt, grid_cap, persistent, staged)
+    _check(lib().cfd_filter_ex(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
+                               _ptr(mu), ctypes.byref(o), _stream(stream)))
+    return mu
+
+
+def cfd_workspace_status(work, stream=None):
+    """Device status of a filter workspace (raises CfdError on a recorded timeout)."""
+    _check(lib().cfd_workspace_status(_ptr(work), _stream(stream)))
+
+
+def cfd_kpm_moments(H, lmin, lmax, n_p, R, n_b, work=None, stream=None):
+    """[n_s, 2 n_p] Chebyshev moments of the columns of R (not modified)."""
+    blk = block_of(R)
+    ws = cfd_filter_workspace(H.N, blk.n_cols, n_b, n_p, H.prec, blk.prec)
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, R.device)
+    mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=R.device)
+    _check(lib().cfd_kpm_moments(H.ref(), lmin, lmax, n_p, blk, n_b, _ptr(work), work.numel(), _ptr(mu),
+                                 _stream(stream)))
+    return mu
+
+
+def cfd_kpm_count(mu, N, lmin, lmax, lam_l, lam_r):
+    """Estimated eigenvalue count in [lam_l, lam_r] from host moments mu [n_vec, n_mom]."""
+    import numpy as np
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    out = ctypes.c_double()
+    _check(lib().cfd_kpm_count(m.ctypes.data_as(ctypes.c_void_p), m.shape[0], m.shape[1], N, lmin, lmax, lam_l,
+                               lam_r, ctypes.byref(out)))
+    return out.value
+
+
+def cfd_kpm_window(mu, N, lmin, lmax, center, target):
+    """(lam_l, lam_r) centred at `center` whose KPM count is `target`."""
+    import numpy as np
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib().cfd_kpm_window(m.ctypes.data_as(ctypes.c_void_p), m.shape[0], m.shape[1], N, lmin, lmax, center,
+                                target, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+class Batch(Matrix):
+    """A built batch: the block-diagonal matrix, its chunk -> realisation map and row offsets."""
+
+    def __init__(self, cmat, buffers, params, chunk_rid, row_off):
+        super().__init__(cmat, buffers, params)
+        self.chunk_rid = chunk_rid
+        self.row_off = row_off
+        self.R = len(row_off) - 1
+
+
+def cfd_build_batch(params_list, C=32, sigma=1, prec="c128", device="cuda", stream=None):
+    """Build R realisations (list of cfd_topi_params) as one block-diagonal matrix."""
+    import numpy as np
+    prec = _prec(prec)
+    R = len(params_list)
+    P = (cfd_topi_params * R)(*params_list)
+    sz = cfd_matrix_sizes()
+    off = np.zeros(R + 1, dtype=np.int64)
+    _check(lib().cfd_batch_query_size(P, R, C, sigma, prec, ctypes.byref(sz), off.ctypes.data_as(ctypes.c_void_p)))
+    dev = torch.device(device)
+    bufs = {
+        "val": _workspace(sz.bytes_val, dev), "col": _workspace(sz.bytes_col, dev),
+        "chunk_ptr": _workspace(sz.bytes_chunk_ptr, dev), "chunk_len": _workspace(sz.bytes_chunk_len, dev),
+        "perm": _workspace(sz.bytes_perm, dev) if sz.bytes_perm else None,
+        "work": _workspace(sz.bytes_work, dev),
+    }
+    rid = torch.empty(sz.n_chunks, dtype=torch.int32, device=dev)
+    b = cfd_matrix_buffers(*[(bufs[k].data_ptr() if bufs[k] is not None else None)
+                             for k in ("val", "col", "chunk_ptr", "chunk_len", "perm", "work")])
+    out = cfd_matrix()
+    _check(lib().cfd_build_batch(P, R, C, sigma, prec, ctypes.byref(b), _ptr(rid), ctypes.byref(out),
+                                 _stream(stream)))
+    return Batch(out, bufs, list(params_list), rid, off)
+
+
+def cfd_filter_batched(B, windows, n_p, X, n_b, persistent=1, vpt=0, work=None, stream=None):
+    """Filter every realisation of batch B at once; windows: float64 device tensor [R, 4]
+    (lmin, lmax, lam_l, lam_r per realisation)."""
+    blk = block_of(X)
+    ws = lib().cfd_filter_batched_workspace(B.N, B.R, blk.n_cols, n_b, n_p, B.prec, blk.prec)
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, X.device)
+    o = cfd_filter_opts(vpt, 0, persistent)
+    _check(lib().cfd_filter_batched(B.ref(), _ptr(B.chunk_rid), B.R, _ptr(windows), n_p, blk, n_b, _ptr(work),
+                                    work.numel(), ctypes.byref(o), _stream(stream)))
 
 
 # ------------------------------------------------------- bounds, dense --
@@ -356,6 +504,44 @@ def cfd_solve(H, X, lam_l, lam_r, n_p, n_b, H_low=None, policy=CFD_POLICY_FP64, 
     if st != 0 and (raise_noconv or st != 6):
         _check(st)
     return ev, rs, res
+
+
+def batch_row_end(B):
+    """End of each realisation's real rows in a batch."""
+    import numpy as np
+    return np.array([B.row_off[r] + 4 * p.Nx * p.Ny * p.Nz for r, p in enumerate(B.params)], dtype=np.int64)
+
+
+def cfd_solve_batched(B, X, windows, n_t, n_p, n_b, B_low=None, policy=CFD_POLICY_FP64, tol=1e-10, max_iter=50,
+                      seed=2, start=0, switch_tol=0.0, work=None, stream=None, raise_noconv=True):
+    """Batched ChebFD solve.  windows: host array [R, 4]; n_t: host ints [R].
+    Returns (evals [R, n_s], resid [R, n_s], list of cfd_solve_result)."""
+    import numpy as np
+    blk = block_of(X)
+    R = B.R
+    win = np.ascontiguousarray(windows, dtype=np.float64).reshape(R, 4)
+    nt = np.ascontiguousarray(n_t, dtype=np.int32).reshape(R)
+    off = np.ascontiguousarray(B.row_off, dtype=np.int64)
+    end = batch_row_end(B)
+    p = cfd_solve_params(lam_l=0, lam_r=0, lmin=0, lmax=0, tol=tol, switch_tol=switch_tol, seed=seed,
+                         n_s=blk.n_cols, n_p=n_p, n_b=n_b, n_t=0, max_iter=max_iter, policy=policy,
+                         bounds_steps=0, start=start)
+    ws = lib().cfd_solve_batched_workspace(B.ref(), R, ctypes.byref(p))
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, X.device)
+    ev = np.zeros((R, blk.n_cols))
+    rs = np.zeros((R, blk.n_cols))
+    res = (cfd_solve_result * R)()
+
+    def vp(a):
+        return a.ctypes.data_as(ctypes.c_void_p)
+
+    st = lib().cfd_solve_batched(B.ref(), B_low.ref() if B_low is not None else None, _ptr(B.chunk_rid), R,
+                                 vp(off), vp(end), vp(win), vp(nt), ctypes.byref(p), blk, vp(ev), vp(rs), res,
+                                 _ptr(work), work.numel(), _stream(stream))
+    if st != 0 and (raise_noconv or st != 6):
+        _check(st)
+    return ev, rs, list(res)
 
 
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024

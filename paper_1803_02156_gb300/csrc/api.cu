@@ -1,4 +1,5 @@
 // Status strings, per-thread error messages, device queries, prefix scan.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -8,6 +9,9 @@
 namespace cfd {
 
 static thread_local char g_last_error[512] = {0};
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 cfd_status fail(cfd_status st, const char *fmt, ...) {
     va_list ap;
@@ -128,8 +132,11 @@ cfd_status exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *
     int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     int64_t *ts = static_cast<int64_t *>(work);
     scan_tile_sums<<<(unsigned)tiles, SCAN_THREADS, 0, stream>>>(in, n, ts);
+    CFD_COUNT_LAUNCH();
     scan_tile_offsets<<<1, SCAN_THREADS, 0, stream>>>(ts, tiles);
+    CFD_COUNT_LAUNCH();
     scan_apply<<<(unsigned)tiles, SCAN_THREADS, 0, stream>>>(in, n, ts, out);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;
 }
@@ -155,5 +162,7 @@ const char *cfd_status_string(int status) {
 const char *cfd_last_error(void) { return cfd::g_last_error; }
 
 const char *cfd_version(void) { return "1.0.0"; }
+
+unsigned long long cfd_launch_count(void) { return cfd::g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -38,6 +38,10 @@ void clear_error();
         if (s_ != CFD_OK) return s_;                                                \
     } while (0)
 
+// Every kernel the library launches is counted (cfd_launch_count()).
+void count_launch();
+#define CFD_COUNT_LAUNCH() ::cfd::count_launch()
+
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -89,19 +93,24 @@ __device__ __forceinline__ void cfma(C &acc, const C h, const C v) {
 
 template <typename T>
 struct SellView {
-    const cplx_t<T> *val;
+    const cplx_t<T> *val;     // complex values (packed == false)
+    const T *pval;            // packed: one real scalar per slot (packed == true)
+    bool packed;
     const int32_t *col;
     const int64_t *chunk_ptr;
-    const int32_t *chunk_len;
+    const int32_t *chunk_len;  // packed: real slot count | imaginary slot count << 16
     const int32_t *perm;  // sorted row -> canonical row, nullptr when sigma == 1
     int64_t n_rows;
     int log2C;
+    int slots_bound;          // upper bound on slots per row of any chunk (0: unknown)
 };
 
 template <typename T>
 inline SellView<T> sell_view(const cfd_matrix *H) {
     SellView<T> v;
-    v.val = static_cast<const cplx_t<T> *>(H->val);
+    v.packed = (H->flags & CFD_MATRIX_PACKED) != 0;
+    v.val = v.packed ? nullptr : static_cast<const cplx_t<T> *>(H->val);
+    v.pval = v.packed ? static_cast<const T *>(H->val) : nullptr;
     v.col = H->col;
     v.chunk_ptr = H->chunk_ptr;
     v.chunk_len = H->chunk_len;
@@ -110,6 +119,7 @@ inline SellView<T> sell_view(const cfd_matrix *H) {
     int l = 0;
     while ((1 << l) < H->C) ++l;
     v.log2C = l;
+    v.slots_bound = (H->flags >> CFD_MATRIX_SLOTS_SHIFT) & 0xff;
     return v;
 }
 

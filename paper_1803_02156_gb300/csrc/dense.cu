@@ -33,17 +33,30 @@ constexpr int GR_LDS = GR_TILE + 4;  // smem row stride (doubles), conflict-free
 constexpr int GR_THREADS = 256;
 
 // Partial real Gram of a K-range: part[split][m][n] = sum_k A[k][m0 + m] B[k][n0 + n]
-// over rows k of this split.  grid = (tiles_m * tiles_n, splits).
+// over rows k of this split.  grid = (tiles_m * tiles_n, splits[, R]).  With
+// row_off (batch), grid.z indexes the realisation whose rows
+// [row_off[z], row_off[z+1]) are split evenly.
 __global__ void __launch_bounds__(GR_THREADS)
 k_gram(const double *__restrict__ A, int64_t lda, int ma, const double *__restrict__ B, int64_t ldb,
-       int nb, int64_t K, int64_t rows_per_split, double *part) {
+       int nb, int64_t K, int64_t rows_per_split, double *part, const int64_t *row_off) {
     __shared__ __align__(16) double As[GR_KS][GR_LDS];
     __shared__ __align__(16) double Bs[GR_KS][GR_LDS];
     const int tiles_n = (nb + GR_TILE - 1) / GR_TILE;
     const int m0 = (blockIdx.x / tiles_n) * GR_TILE;
     const int n0 = (blockIdx.x % tiles_n) * GR_TILE;
-    const int64_t k_begin = (int64_t)blockIdx.y * rows_per_split;
-    const int64_t k_end = min(K, k_begin + rows_per_split);
+    int64_t k_begin, k_end;
+    double *out;
+    if (row_off) {
+        const int64_t r0 = row_off[blockIdx.z], r1 = row_off[blockIdx.z + 1];
+        const int64_t rps = ((r1 - r0 + gridDim.y - 1) / gridDim.y + GR_KS - 1) / GR_KS * GR_KS;
+        k_begin = r0 + (int64_t)blockIdx.y * rps;
+        k_end = min(r1, k_begin + rps);
+        out = part + ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * ma * nb;
+    } else {
+        k_begin = (int64_t)blockIdx.y * rows_per_split;
+        k_end = min(K, k_begin + rows_per_split);
+        out = part + (int64_t)blockIdx.y * ma * nb;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wm = (warp >> 2) * 32;   // warp tile: 32 rows (4 m-tiles) x 16 cols (2 n-tiles)
     const int wn = (warp & 3) * 16;
@@ -77,7 +90,6 @@ k_gram(const double *__restrict__ A, int64_t lda, int ma, const double *__restri
         }
         __syncthreads();
     }
-    double *out = part + (int64_t)blockIdx.y * ma * nb;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -90,11 +102,16 @@ k_gram(const double *__restrict__ A, int64_t lda, int ma, const double *__restri
             }
 }
 
-// S[a][b] (complex, ld lds) = sum over splits (fixed order) of the real Gram, folded.
-__global__ void k_gram_fold(const double *part, int splits, int ma, int nb, double2 *S, int64_t lds) {
+// S[a][b] (complex, ld lds) = sum over splits (fixed order) of the real Gram,
+// folded; grid.y = realisation in a batch (S advanced by s_stride, part by
+// splits * ma * nb).
+__global__ void k_gram_fold(const double *part, int splits, int ma, int nb, double2 *S, int64_t lds,
+                            int64_t s_stride) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int na = ma / 2, nbc = nb / 2;
     if (e >= na * nbc) return;
+    part += (int64_t)blockIdx.y * splits * ma * nb;
+    S += (int64_t)blockIdx.y * s_stride;
     int a = e / nbc, b = e % nbc;
     double g00 = 0, g11 = 0, g01 = 0, g10 = 0;
     for (int s = 0; s < splits; ++s) {
@@ -131,10 +148,43 @@ cfd_status gram(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t
     int tiles = ((ma + GR_TILE - 1) / GR_TILE) * ((nb + GR_TILE - 1) / GR_TILE);
     dim3 grid(tiles, std::max(splits, 1));
     k_gram<<<grid, GR_THREADS, 0, stream>>>(reinterpret_cast<const double *>(X), 2 * ldx, ma,
-                                           reinterpret_cast<const double *>(Y), 2 * ldy, nb, K, rps, work);
+                                           reinterpret_cast<const double *>(Y), 2 * ldy, nb, K, rps, work, nullptr);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     int n = na * nbc;
-    k_gram_fold<<<(n + 255) / 256, 256, 0, stream>>>(work, std::max(splits, 1), ma, nb, S, lds);
+    k_gram_fold<<<(n + 255) / 256, 256, 0, stream>>>(work, std::max(splits, 1), ma, nb, S, lds, 0);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    return CFD_OK;
+}
+
+// ----------------------------------------------------------- batched Gram --
+
+int gram_batched_splits(int R, int ma, int nb) {
+    int tiles = ((ma + GR_TILE - 1) / GR_TILE) * ((nb + GR_TILE - 1) / GR_TILE);
+    return std::max(1, std::min(GRAM_MAX_SPLITS, GRAM_TARGET_CTAS / (tiles * R)));
+}
+
+size_t gram_batched_workspace(int R, int na, int nbc) {
+    int ma = 2 * na, nb = 2 * nbc;
+    return round_up((size_t)R * gram_batched_splits(R, ma, nb) * ma * nb * sizeof(double), 256);
+}
+
+cfd_status gram_batched(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nbc,
+                        const int64_t *row_off_dev, int R, double2 *S, int64_t lds, int64_t s_stride, double *work,
+                        cudaStream_t stream) {
+    int ma = 2 * na, nb = 2 * nbc;
+    int splits = gram_batched_splits(R, ma, nb);
+    int tiles = ((ma + GR_TILE - 1) / GR_TILE) * ((nb + GR_TILE - 1) / GR_TILE);
+    dim3 grid(tiles, splits, R);
+    k_gram<<<grid, GR_THREADS, 0, stream>>>(reinterpret_cast<const double *>(X), 2 * ldx, ma,
+                                           reinterpret_cast<const double *>(Y), 2 * ldy, nb, 0, 0, work,
+                                           row_off_dev);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    int n = na * nbc;
+    k_gram_fold<<<dim3((n + 255) / 256, R), 256, 0, stream>>>(work, splits, ma, nb, S, lds, s_stride);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;
 }
@@ -151,6 +201,8 @@ constexpr int PJ_THREADS = 256;
 __global__ void k_real_rep(const double2 *M, int64_t ldm, int n_in, int n_out, double *Mr) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_in * n_out) return;
+    M += (int64_t)blockIdx.y * n_in * ldm;                     // batch: one matrix per realisation
+    Mr += (int64_t)blockIdx.y * (2 * n_in) * (2 * n_out);
     int a = e / n_out, b = e % n_out;
     double2 z = M[(int64_t)a * ldm + b];
     int64_t W = 2 * n_out;
@@ -165,8 +217,19 @@ __global__ void k_real_rep(const double2 *M, int64_t ldm, int n_in, int n_out, d
 // no other CTA touches those rows.  Dynamic smem: PJ_ROWS * (2 n_in + 4) doubles
 // for the rows plus a PJ_KS x (PJ_NT + 4) slab of Mr.
 __global__ void __launch_bounds__(PJ_THREADS)
-k_project(double *X, int64_t ldx, int kin, int nout, const double *__restrict__ Mr, int64_t n_rows) {
+k_project(double *X, int64_t ldx, int kin, int nout, const double *__restrict__ Mr, int64_t n_rows,
+          const int64_t *row_off, int R) {
     extern __shared__ __align__(16) double sm[];
+    if (row_off) {        // batch: this panel's realisation (panels never straddle two)
+        const int64_t r0 = (int64_t)blockIdx.x * PJ_ROWS;
+        int lo = 0, hi = R - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) / 2;
+            if (row_off[mid] <= r0) lo = mid;
+            else hi = mid - 1;
+        }
+        Mr += (int64_t)lo * kin * nout;
+    }
     const int lda = kin + 4;
     double *Xs = sm;                              // [PJ_ROWS][lda]
     double *Ms = sm + (size_t)PJ_ROWS * lda;      // [PJ_KS][PJ_NT + 4]
@@ -230,6 +293,7 @@ cfd_status project_inplace(double2 *X, int64_t ldx, int64_t n_rows, int n_in, co
     if (n_out > n_in) return fail(CFD_ERR_ARG, "in-place projection cannot widen (%d -> %d)", n_in, n_out);
     int n = n_in * n_out;
     k_real_rep<<<(n + 255) / 256, 256, 0, stream>>>(M, ldm, n_in, n_out, work);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     int kin = 2 * n_in, nout = 2 * n_out;
     size_t smem = ((size_t)PJ_ROWS * (kin + 4) + (size_t)PJ_KS * (PJ_NT + 4)) * sizeof(double);
@@ -243,10 +307,35 @@ cfd_status project_inplace(double2 *X, int64_t ldx, int64_t n_rows, int n_in, co
     if (smem > 227 * 1024) return fail(CFD_ERR_ARG, "block too wide for in-place projection (n=%d)", n_in);
     unsigned grid = (unsigned)((n_rows + PJ_ROWS - 1) / PJ_ROWS);
     k_project<<<grid, PJ_THREADS, smem, stream>>>(reinterpret_cast<double *>(X), 2 * ldx, kin, nout, work,
-                                                  n_rows);
+                                                  n_rows, nullptr, 0);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;
 }
+
+// X_r <- X_r M_r for every realisation r of a batch (M: R matrices n x n,
+// stride m_stride), in place.  Panel rows must not straddle realisations
+// (row offsets are multiples of 32).
+cfd_status project_batched(double2 *X, int64_t ldx, int64_t n_rows, int n, const double2 *M, int64_t ldm,
+                           int64_t m_stride, const int64_t *row_off_dev, int R, double *work, cudaStream_t stream) {
+    if (m_stride != (int64_t)n * ldm) return fail(CFD_ERR_ARG, "batched projection needs packed matrices");
+    int nn = n * n;
+    k_real_rep<<<dim3((nn + 255) / 256, R), 256, 0, stream>>>(M, ldm, n, n, work);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    int kin = 2 * n;
+    size_t smem = ((size_t)PJ_ROWS * (kin + 4) + (size_t)PJ_KS * (PJ_NT + 4)) * sizeof(double);
+    if (smem > 227 * 1024) return fail(CFD_ERR_ARG, "block too wide for in-place projection (n=%d)", n);
+    CFD_CUDA(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    unsigned grid = (unsigned)((n_rows + PJ_ROWS - 1) / PJ_ROWS);
+    k_project<<<grid, PJ_THREADS, smem, stream>>>(reinterpret_cast<double *>(X), 2 * ldx, kin, kin, work, n_rows,
+                                                  row_off_dev, R);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    return CFD_OK;
+}
+
+size_t project_batched_workspace(int R, int n) { return round_up((size_t)R * (2 * n) * (2 * n) * sizeof(double), 256); }
 
 // ------------------------------------------------------ Jacobi eigensolver --
 
@@ -449,6 +538,7 @@ cfd_status eigh(const double2 *A, int64_t lda, int n, double *evals, double2 *Q,
     int *sw = c.take<int>(64);
     int64_t nn = (int64_t)n * n;
     k_copy_sym<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(A, lda, n, W);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     // grid: one CTA for small problems, more for large (all co-resident)
     const int threads = 512;
@@ -461,9 +551,154 @@ cfd_status eigh(const double2 *A, int64_t lda, int n, double *evals, double2 *Q,
     int max_sweeps = 40;
     void *args[] = {&W, &V, &n, &tol, &max_sweeps, &rot, &part, &sw};
     CFD_CUDA(cudaLaunchCooperativeKernel((void *)k_jacobi, dim3(blocks), dim3(threads), args, 0, stream));
+    CFD_COUNT_LAUNCH();
     k_eig_sort<<<(n + 127) / 128, 128, 0, stream>>>(W, V, n, evals, Q, ldq);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     if (sweeps) CFD_CUDA(cudaMemcpyAsync(sweeps, sw, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    return CFD_OK;
+}
+
+// ------------------------------------------------- batched small Jacobi --
+
+// One CTA per problem: cyclic Jacobi (same rotations as k_jacobi) on a
+// complex Hermitian n x n matrix (n <= 64) held with its eigenvectors in
+// shared memory.  Problem b reads the Hermitian part of A + b a_stride and
+// writes ascending eigenvalues to evals + b n and eigenvectors (columns) to
+// Q + b q_stride.
+__global__ void __launch_bounds__(256)
+k_jacobi_blocks(const double2 *A, int64_t lda, int64_t a_stride, int n, double tol, int max_sweeps,
+                double *evals, double2 *Q, int64_t ldq, int64_t q_stride, int *sweeps_out) {
+    extern __shared__ __align__(16) double2 shj[];
+    double2 *W = shj, *V = shj + n * n;
+    __shared__ double4 rot[DENSE_BATCH_MAX_N / 2 + 1];
+    __shared__ double red[2][256 / 32];
+    __shared__ int done;
+    const int m = n + (n & 1), npairs = m / 2;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    A += (int64_t)blockIdx.x * a_stride;
+    for (int e = tid; e < n * n; e += nthr) {
+        int i = e / n, j = e % n;
+        double2 a = A[(int64_t)i * lda + j], b = A[(int64_t)j * lda + i];
+        W[e] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+        V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int e = tid; e < n * n; e += nthr) {
+            double q = W[e].x * W[e].x + W[e].y * W[e].y;
+            tot += q;
+            if (e / n != e % n) off += q;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if ((tid & 31) == 0) {
+            red[0][tid >> 5] = off;
+            red[1][tid >> 5] = tot;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double so = 0, st = 0;
+            for (int w = 0; w < (nthr >> 5); ++w) {
+                so += red[0][w];
+                st += red[1][w];
+            }
+            done = (so <= tol * tol * st || so == 0.0);
+        }
+        __syncthreads();
+        if (done) break;
+        for (int r = 0; r < m - 1; ++r) {
+            for (int k = tid; k < npairs; k += nthr) {
+                int p = rr_player(k, r, m), q = rr_player(m - 1 - k, r, m);
+                if (p > q) { int t2 = p; p = q; q = t2; }
+                double4 R = make_double4(1.0, 0.0, 0.0, 0.0);
+                if (q < n) {
+                    double2 apq = W[p * n + q];
+                    double g = sqrt(apq.x * apq.x + apq.y * apq.y);
+                    double app = W[p * n + p].x, aqq = W[q * n + q].x;
+                    if (g > 0.0) {
+                        double tau = (aqq - app) / (2.0 * g);
+                        double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                        R = make_double4(c, sn * apq.x / g, sn * apq.y / g, t * g);
+                    }
+                }
+                rot[k] = R;
+            }
+            __syncthreads();
+            for (int e = tid; e < npairs * n; e += nthr) {          // rows p, q
+                int k = e / n, col = e % n;
+                int p = rr_player(k, r, m), q = rr_player(m - 1 - k, r, m);
+                if (p > q) { int t2 = p; p = q; q = t2; }
+                if (q >= n) continue;
+                double4 R = rot[k];
+                if (R.y == 0.0 && R.z == 0.0) continue;
+                double2 ap = W[p * n + col], aq = W[q * n + col];
+                W[p * n + col] = make_double2(R.x * ap.x - (R.y * aq.x - R.z * aq.y),
+                                              R.x * ap.y - (R.y * aq.y + R.z * aq.x));
+                W[q * n + col] = make_double2((R.y * ap.x + R.z * ap.y) + R.x * aq.x,
+                                              (R.y * ap.y - R.z * ap.x) + R.x * aq.y);
+            }
+            __syncthreads();
+            for (int e = tid; e < 2 * npairs * n; e += nthr) {      // columns p, q of W and V
+                int which = e / (npairs * n), f = e % (npairs * n);
+                int k = f / n, row = f % n;
+                int p = rr_player(k, r, m), q = rr_player(m - 1 - k, r, m);
+                if (p > q) { int t2 = p; p = q; q = t2; }
+                if (q >= n) continue;
+                double4 R = rot[k];
+                if (R.y == 0.0 && R.z == 0.0) continue;
+                double2 *M = which ? V : W;
+                double2 ap = M[row * n + p], aq = M[row * n + q];
+                M[row * n + p] = make_double2(R.x * ap.x - (R.y * aq.x + R.z * aq.y),
+                                              R.x * ap.y - (R.y * aq.y - R.z * aq.x));
+                M[row * n + q] = make_double2((R.y * ap.x - R.z * ap.y) + R.x * aq.x,
+                                              (R.y * ap.y + R.z * ap.x) + R.x * aq.y);
+            }
+            __syncthreads();
+            for (int k = tid; k < npairs; k += nthr) {               // exact 2x2 blocks
+                int p = rr_player(k, r, m), q = rr_player(m - 1 - k, r, m);
+                if (p > q) { int t2 = p; p = q; q = t2; }
+                if (q >= n) continue;
+                double4 R = rot[k];
+                if (R.y == 0.0 && R.z == 0.0) continue;
+                W[p * n + q] = make_double2(0.0, 0.0);
+                W[q * n + p] = make_double2(0.0, 0.0);
+                W[p * n + p].y = 0.0;
+                W[q * n + q].y = 0.0;
+            }
+            __syncthreads();
+        }
+    }
+    // ascending eigenvalues (stable by index) and their eigenvectors
+    evals += (int64_t)blockIdx.x * n;
+    Q += (int64_t)blockIdx.x * q_stride;
+    for (int i = tid; i < n; i += nthr) {
+        double li = W[i * n + i].x;
+        int rank = 0;
+        for (int j = 0; j < n; ++j) {
+            double lj = W[j * n + j].x;
+            if (lj < li || (lj == li && j < i)) ++rank;
+        }
+        evals[rank] = li;
+        for (int k = 0; k < n; ++k) Q[(int64_t)k * ldq + rank] = V[k * n + i];
+    }
+    if (tid == 0 && sweeps_out) sweeps_out[blockIdx.x] = sweep;
+}
+
+cfd_status eigh_batched(const double2 *A, int64_t lda, int64_t a_stride, int n, int R, double *evals, double2 *Q,
+                        int64_t ldq, int64_t q_stride, cudaStream_t stream) {
+    if (n < 1 || n > DENSE_BATCH_MAX_N) return fail(CFD_ERR_ARG, "batched eigensolver needs 1 <= n <= %d", DENSE_BATCH_MAX_N);
+    size_t smem = (size_t)2 * n * n * sizeof(double2);
+    CFD_CUDA(cudaFuncSetAttribute(k_jacobi_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    double tol = 2.220446049250313e-16 * std::max(n, 4);
+    k_jacobi_blocks<<<R, 256, smem, stream>>>(A, lda, a_stride, n, tol, 40, evals, Q, ldq, q_stride, nullptr);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
     return CFD_OK;
 }
 
@@ -475,9 +710,19 @@ constexpr int RS_THREADS = 256;
 // nullable: plain column norms of Z).
 __global__ void __launch_bounds__(RS_THREADS)
 k_resid_part(const double2 *Z, int64_t ldz, const double2 *X, int64_t ldx, const double *theta, int n,
-             int64_t n_rows, int64_t rows_per_cta, double *part) {
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
-    const int64_t r1 = min(n_rows, r0 + rows_per_cta);
+             int64_t n_rows, int64_t rows_per_cta, double *part, const int64_t *row_off) {
+    int64_t r0, r1;
+    if (row_off) {        // batch: grid.y = realisation, its rows split over grid.x CTAs
+        const int64_t a = row_off[blockIdx.y], e = row_off[blockIdx.y + 1];
+        const int64_t rpc = (e - a + gridDim.x - 1) / gridDim.x;
+        r0 = a + (int64_t)blockIdx.x * rpc;
+        r1 = min(e, r0 + rpc);
+        theta += (int64_t)blockIdx.y * n;
+        part += (int64_t)blockIdx.y * gridDim.x * n;
+    } else {
+        r0 = (int64_t)blockIdx.x * rows_per_cta;
+        r1 = min(n_rows, r0 + rows_per_cta);
+    }
     __shared__ double red[RS_THREADS];
     for (int j0 = 0; j0 < n; j0 += 32) {
         const int j = j0 + (threadIdx.x & 31);
@@ -506,6 +751,8 @@ k_resid_part(const double2 *Z, int64_t ldz, const double2 *X, int64_t ldx, const
 __global__ void k_resid_fold(const double *part, int ctas, int n, double *out) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    part += (int64_t)blockIdx.y * ctas * n;                  // batch: one fold per realisation
+    out += (int64_t)blockIdx.y * n;
     double s = 0.0;
     for (int b = 0; b < ctas; ++b) s += part[(int64_t)b * n + j];
     out[j] = sqrt(s);
@@ -519,11 +766,28 @@ cfd_status resid_norms(const double2 *Z, int64_t ldz, const double2 *X, int64_t 
     ctas = std::min<int64_t>(ctas, 4LL * sm_count());
     int64_t rpc = (n_rows + ctas - 1) / ctas;
     ctas = (n_rows + rpc - 1) / rpc;
-    k_resid_part<<<(unsigned)ctas, RS_THREADS, 0, stream>>>(Z, ldz, X, ldx, theta, n, n_rows, rpc, work);
+    k_resid_part<<<(unsigned)ctas, RS_THREADS, 0, stream>>>(Z, ldz, X, ldx, theta, n, n_rows, rpc, work, nullptr);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     k_resid_fold<<<(n + 127) / 128, 128, 0, stream>>>(work, (int)ctas, n, out);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;
 }
+
+cfd_status resid_norms_batched(const double2 *Z, int64_t ldz, const double2 *X, int64_t ldx, const double *theta,
+                               int n, const int64_t *row_off_dev, int R, double *out, double *work,
+                               cudaStream_t stream) {
+    const int per = 8;     // CTAs per realisation
+    k_resid_part<<<dim3(per, R), RS_THREADS, 0, stream>>>(Z, ldz, X, ldx, theta, n, 0, 0, work, row_off_dev);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    k_resid_fold<<<dim3((n + 127) / 128, R), 128, 0, stream>>>(work, per, n, out);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    return CFD_OK;
+}
+
+size_t resid_batched_workspace(int R, int n) { return round_up((size_t)R * 8 * n * sizeof(double), 256); }
 
 }  // namespace cfd

@@ -9,6 +9,7 @@ constexpr int GRAM_MAX_SPLITS = 256;   // K-splits of a Gram (partials in the wo
 constexpr int GRAM_TARGET_CTAS = 640;  // CTAs per Gram launch (about 4 per SM)
 constexpr int RESID_MAX_CTAS = 1024;
 constexpr int DENSE_MAX_COLS = 256;     // widest block for Gram / projection / Jacobi
+constexpr int DENSE_BATCH_MAX_N = 64;   // widest block per realisation in batched dense kernels
 
 // S (na x nb complex, ld lds) = X^H Y for N x na and N x nb blocks (unit column
 // stride, ld in complex elements).  Deterministic (fixed-order split reduction).
@@ -32,5 +33,21 @@ cfd_status eigh(const double2 *A, int64_t lda, int n, double *evals, double2 *Q,
 size_t resid_workspace(int n);
 cfd_status resid_norms(const double2 *Z, int64_t ldz, const double2 *X, int64_t ldx, const double *theta, int n,
                        int64_t n_rows, double *out, double *work, cudaStream_t stream);
+
+// Batched forms (realisation r owns rows [row_off[r], row_off[r+1]), device
+// row_off; per-realisation outputs are stacked with the given strides).
+size_t gram_batched_workspace(int R, int na, int nb);
+cfd_status gram_batched(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nb,
+                        const int64_t *row_off_dev, int R, double2 *S, int64_t lds, int64_t s_stride, double *work,
+                        cudaStream_t stream);
+size_t project_batched_workspace(int R, int n);
+cfd_status project_batched(double2 *X, int64_t ldx, int64_t n_rows, int n, const double2 *M, int64_t ldm,
+                           int64_t m_stride, const int64_t *row_off_dev, int R, double *work, cudaStream_t stream);
+cfd_status eigh_batched(const double2 *A, int64_t lda, int64_t a_stride, int n, int R, double *evals, double2 *Q,
+                        int64_t ldq, int64_t q_stride, cudaStream_t stream);
+size_t resid_batched_workspace(int R, int n);
+cfd_status resid_norms_batched(const double2 *Z, int64_t ldz, const double2 *X, int64_t ldx, const double *theta,
+                               int n, const int64_t *row_off_dev, int R, double *out, double *work,
+                               cudaStream_t stream);
 
 }  // namespace cfd

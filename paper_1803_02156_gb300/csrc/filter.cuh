@@ -26,8 +26,10 @@ struct StepArgs {
     int64_t ldin;
     cplx_t<T> *w;           // output (read as V_prev in general steps)
     int64_t ldw;
-    cplx_t<T> *x;           // accumulator X (steps 2..n_p)
+    cplx_t<T> *x;           // accumulator X (steps 2..n_p); nullptr: moments only
     int64_t ldx;
+    const cplx_t<T> *x0 = nullptr;   // moments only: the start block (read by step 2)
+    int64_t ldx0 = 0;
     double a;               // alpha in step 1, 2 alpha afterwards
     double beta;            // centre of the spectral interval
     const double *gc;       // weights g_k c_k, k = 0..n_p (device)
@@ -35,18 +37,52 @@ struct StepArgs {
     double *partial;        // per-CTA partial dots [grid][nb][2]
     unsigned *ticket;       // CTA completion counter, zero between launches
     double *dots;           // reduced dots of this step [nb][2]
+    // batch of realisations (null for a single matrix): chunk -> realisation,
+    // per realisation {alpha, beta, g_0 c_0, ..., g_np c_np} with stride rcoef_ld
+    const int32_t *chunk_rid = nullptr;
+    const double *rcoef = nullptr;
+    int64_t rcoef_ld = 0;
+    // general steps staged through shared memory by TMA (k_cheb_step_staged);
+    // status receives CFD_ERR_TIMEOUT if one of its bounded waits expires
+    int staged = 0;
+    int *status = nullptr;
 };
 
 template <typename T>
 cfd_status launch_step(int kind, int nb, int vpt, const StepArgs<T> &A, int grid_cap,
                        cudaStream_t stream);
+// Per (precision, value storage) instantiations, in step_*.cu.
+template <typename T, bool PACK>
+cfd_status launch_step_p(int kind, int nb, int vpt, const StepArgs<T> &A, int grid_cap, cudaStream_t s);
+template <typename T, bool PACK>
+cfd_status launch_persistent_p(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> *xb,
+                               int64_t ldx, int n_p, int grid_cap, cudaStream_t s);
+
+template <typename T>
+cfd_status launch_persistent(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> *xb,
+                             int64_t ldx, int n_p, int grid_cap, cudaStream_t stream);
+
+// How one filter application is run.
+struct FilterPlan {
+    int n_b = 0, n_p = 0, vpt = 0, grid_cap = 0;
+    bool persistent = false;
+    int staged = 0;
+    double alpha = 0, beta = 0;
+    const int32_t *chunk_rid = nullptr;   // batch: chunk -> realisation
+    const double *rcoef = nullptr;        // batch: per realisation {alpha, beta, weights}
+    int64_t rcoef_ld = 0;
+};
 
 struct FilterScratch {
+    int *status;            // device status word (first bytes of the workspace)
     void *va, *vb, *xn;
     double *gc, *raw, *partial;
     unsigned *ticket;
     int grid_cap;
 };
+
+// Whether the general steps default to the TMA-staged kernel for a matrix precision.
+bool default_staged(int prec);
 
 int default_vpt(int prec, int n_b);
 size_t filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X);
@@ -59,6 +95,16 @@ cfd_status launch_narrow(const double2 *src, int64_t lds, float2 *dst, int64_t l
                          int nb, cudaStream_t stream);
 cfd_status launch_widen(const float2 *src, int64_t lds, double2 *dst, int64_t ldd, int64_t n_rows,
                         int nb, cudaStream_t stream);
+// The whole filter with all options (persistent: one cooperative launch per block).
+cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
+                            const cfd_block &X, int n_b, int vpt, int grid_cap, int persistent, int staged,
+                            void *work, size_t work_bytes, double *moments, cudaStream_t stream);
+size_t batched_workspace(int64_t N, int R, int n_s, int n_b, int n_p, int prec_H, int prec_X);
+cfd_status kpm_impl(const cfd_matrix *H, double lmin, double lmax, int n_p, const cfd_block &R, int n_b,
+                    void *work, size_t work_bytes, double *moments, cudaStream_t stream);
+cfd_status filter_batched_impl(const cfd_matrix *H, const int32_t *chunk_rid, int R, const double *windows, int n_p,
+                               const cfd_block &X, int n_b, int vpt, int persistent, void *work, size_t work_bytes,
+                               cudaStream_t stream);
 // The whole filter with explicit tuning knobs (vpt <= 0: default; grid_cap <= 0: none).
 cfd_status filter_impl(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
                        int n_p, const cfd_block &X, int n_b, int vpt, int grid_cap, void *work,

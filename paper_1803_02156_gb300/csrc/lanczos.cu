@@ -49,13 +49,24 @@ __global__ void __launch_bounds__(LZ_THREADS) k_gersh_part(SellView<double> H0, 
         int64_t base = H0.chunk_ptr[ch] + (r & ((1 << H0.log2C) - 1));
         int64_t i = H0.perm ? H0.perm[r] : r;
         double cen = 0.0, rad = 0.0;
-        for (int k = 0; k < H0.chunk_len[ch]; ++k) {
+        const int cl = H0.chunk_len[ch];
+        const int nre = H0.packed ? (cl & 0xffff) : cl;       // packed: real group, then imaginary group
+        const int len = H0.packed ? nre + (cl >> 16) : cl;
+        for (int k = 0; k < len; ++k) {
             int64_t at = base + ((int64_t)k << H0.log2C);
             int c = H0.col[at];
             if (c < 0) continue;
-            C v = val[at];
-            if (c == i) cen += (double)v.x;
-            else rad += sqrt((double)v.x * v.x + (double)v.y * v.y);
+            double re, im;
+            if (H0.packed) {
+                re = k < nre ? H0.pval[at] : 0.0;
+                im = k < nre ? 0.0 : H0.pval[at];
+            } else {
+                C v = val[at];
+                re = v.x;
+                im = v.y;
+            }
+            if (c == i) cen += re;
+            else rad += sqrt(re * re + im * im);
         }
         lo = fmin(lo, cen - rad);
         hi = fmax(hi, cen + rad);
@@ -180,6 +191,7 @@ cfd_status gaussian_block(double2 *X, int64_t ldx, int64_t N, int n, uint64_t se
                           int n_total, cudaStream_t stream) {
     int64_t e = N * n;
     k_gaussian<<<(unsigned)((e + 255) / 256), 256, 0, stream>>>(X, ldx, N, n, seed, tag, col0, n_total);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;
 }
@@ -210,6 +222,7 @@ cfd_status spectral_bounds_dev(const cfd_matrix *H, int steps, uint64_t seed, do
     const int ctas = lz_ctas(N);
     SellView<double> H0 = sell_view<double>(H);
     k_gersh_part<double2><<<ctas, LZ_THREADS, 0, stream>>>(H0, static_cast<const double2 *>(H->val), part + 2048);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     CFD_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), stream));
     // v_0: normalised Gaussian vector
@@ -218,7 +231,9 @@ cfd_status spectral_bounds_dev(const cfd_matrix *H, int steps, uint64_t seed, do
     CFD_CUDA(cudaMemsetAsync(dots, 0, sizeof(double) * 2, stream));
     k_lz_update<<<ctas, LZ_THREADS, 0, stream>>>(v, v, v, dots, beta, 0, N, part);   // alpha = 0: norm only
     k_lz_fold<<<1, 1, 0, stream>>>(part, ctas, beta, steps + 1);
+    CFD_COUNT_LAUNCH();
     k_scale<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(v, N, beta, steps + 1);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     StepArgs<double> A;
     A.H = H0;
@@ -238,8 +253,11 @@ cfd_status spectral_bounds_dev(const cfd_matrix *H, int steps, uint64_t seed, do
         A.dots = dots + 2 * k;                 // (<v, v>, alpha_k = Re <H v, v>)
         CFD_TRY(launch_step<double>(STEP_FIRST, 1, 1, A, 0, stream));
         k_lz_update<<<ctas, LZ_THREADS, 0, stream>>>(w, v, vprev, dots, beta, k, N, part);
+        CFD_COUNT_LAUNCH();
         k_lz_fold<<<1, 1, 0, stream>>>(part, ctas, beta, k);
+        CFD_COUNT_LAUNCH();
         k_scale<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(w, N, beta, k);
+        CFD_COUNT_LAUNCH();
         CFD_LAUNCH_CHECK();
         double2 *t = vprev;
         vprev = v;
@@ -247,9 +265,11 @@ cfd_status spectral_bounds_dev(const cfd_matrix *H, int steps, uint64_t seed, do
         w = t;
     }
     k_lz_tridiag<<<(steps * steps + 255) / 256, 256, 0, stream>>>(dots, beta, steps, T);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     CFD_TRY(eigh(T, steps, steps, theta, Y, steps, ew, ewb, stream, nullptr));
     k_lz_bounds<<<1, 1, 0, stream>>>(theta, Y, steps, beta, part + 2048, ctas, out_dev);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;
 }

@@ -1,5 +1,6 @@
 // Topological-insulator Hamiltonian (Sect. 2.1) built on the device directly
 // into SELL-C-sigma, and canonical CSR export.
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -41,6 +42,21 @@ __host__ __device__ inline int topi_row_len(int64_t i, const Lattice &g) {
         if (g.per[j] || c[j] < g.L[j] - 1) len += 2;
     }
     return len;
+}
+
+// Real and imaginary entries of canonical row i: on-site real; per existing
+// neighbour along x a real diagonal-orbital entry and an imaginary partner,
+// along y two real entries, along z a real and an imaginary entry.
+__host__ __device__ inline void topi_row_counts(int64_t i, const Lattice &g, int *n_re, int *n_im) {
+    int64_t s = i >> 2;
+    int64_t c[3];
+    c[0] = s % g.L[0];
+    c[1] = (s / g.L[0]) % g.L[1];
+    c[2] = s / ((int64_t)g.L[0] * g.L[1]);
+    int nb[3];
+    for (int j = 0; j < 3; ++j) nb[j] = (g.per[j] || c[j] > 0) + (g.per[j] || c[j] < g.L[j] - 1);
+    *n_re = 1 + nb[0] + 2 * nb[1] + nb[2];
+    *n_im = nb[0] + nb[2];
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014): output function and counter-based
@@ -158,20 +174,27 @@ __global__ void k_sigma_sort(Lattice g, int sigma, int32_t *perm) {
     for (int64_t i = r0; i < r1; ++i) perm[r0 + start[topi_row_len(i, g)]++] = (int32_t)i;
 }
 
-__global__ void k_chunk_len(Lattice g, int log2C, int64_t n_chunks, const int32_t *perm,
+// Slots per row of each chunk: the longest row's length, or for packed
+// values the most real entries (low 16 bits) and the most imaginary entries
+// (high 16 bits) of any row.
+__global__ void k_chunk_len(Lattice g, int log2C, int64_t n_chunks, const int32_t *perm, bool packed,
                             int32_t *chunk_len, int64_t *slots) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= n_chunks) return;
     int C = 1 << log2C;
-    int mx = 0;
+    int mx = 0, mre = 0, mim = 0;
     for (int rr = 0; rr < C; ++rr) {
         int64_t r = (c << log2C) + rr;
         if (r >= g.n_rows) break;
         int64_t i = perm ? perm[r] : r;
         mx = max(mx, topi_row_len(i, g));
+        int a, b;
+        topi_row_counts(i, g, &a, &b);
+        mre = max(mre, a);
+        mim = max(mim, b);
     }
-    chunk_len[c] = mx;
-    slots[c] = (int64_t)mx << log2C;
+    chunk_len[c] = packed ? (mre | (mim << 16)) : mx;
+    slots[c] = (int64_t)(packed ? mre + mim : mx) << log2C;
 }
 
 template <typename C>
@@ -199,17 +222,52 @@ __global__ void k_fill(Lattice g, TopiValues v, int log2C, int64_t n_chunks, con
     }
 }
 
+// Packed fill: one real scalar per slot; each row stores its real entries in
+// slots [0, n_re) and its imaginary entries (their imaginary parts) in
+// [n_re, n_re + n_im), both in ascending column order, with n_re, n_im the
+// chunk's maxima (every Topi entry is purely real or purely imaginary).
+template <typename S>
+__global__ void k_fill_packed(Lattice g, TopiValues v, int log2C, int64_t n_chunks, const int32_t *perm,
+                              const int64_t *chunk_ptr, const int32_t *chunk_len, int32_t *col, S *val) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= (n_chunks << log2C)) return;
+    int64_t c = r >> log2C;
+    int64_t rr = r & ((1 << log2C) - 1);
+    int64_t base = chunk_ptr[c] + rr;
+    const int n_re = chunk_len[c] & 0xffff, n_im = chunk_len[c] >> 16;
+    int32_t ec[TOPI_MAX_ROW];
+    double2 ev[TOPI_MAX_ROW];
+    int n = 0;
+    if (r < g.n_rows) n = topi_row(perm ? perm[r] : r, g, v, ec, ev);
+    int kre = 0, kim = n_re;
+    for (int k = 0; k < n; ++k) {
+        bool im = ev[k].y != 0.0;
+        int64_t at = base + ((int64_t)(im ? kim++ : kre++) << log2C);
+        col[at] = ec[k];
+        val[at] = (S)(im ? ev[k].y : ev[k].x);
+    }
+    for (; kre < n_re; ++kre) {
+        col[base + ((int64_t)kre << log2C)] = -1;
+        val[base + ((int64_t)kre << log2C)] = (S)0;
+    }
+    for (; kim < n_re + n_im; ++kim) {
+        col[base + ((int64_t)kim << log2C)] = -1;
+        val[base + ((int64_t)kim << log2C)] = (S)0;
+    }
+}
+
 // CSR export: row lengths of canonical rows, then entries.
 __global__ void k_csr_len(int64_t n_rows, int log2C, const int64_t *chunk_ptr,
-                          const int32_t *chunk_len, const int32_t *perm, const int32_t *col,
+                          const int32_t *chunk_len, const int32_t *perm, const int32_t *col, bool packed,
                           int64_t *rowlen) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_rows) return;
     int64_t c = r >> log2C;
     int64_t base = chunk_ptr[c] + (r & ((1 << log2C) - 1));
+    const int len = packed ? (chunk_len[c] & 0xffff) + (chunk_len[c] >> 16) : chunk_len[c];
     int n = 0;
-    for (int k = 0; k < chunk_len[c]; ++k)
-        if (col[base + ((int64_t)k << log2C)] >= 0) ++n;
+    for (int k = 0; k < len; ++k)
+        if (col[base + ((int64_t)k << log2C)] != -1) ++n;
     rowlen[perm ? perm[r] : r] = n;
 }
 
@@ -233,6 +291,40 @@ __global__ void k_csr_fill(int64_t n_rows, int log2C, const int64_t *chunk_ptr,
     }
 }
 
+// Packed rows back to complex CSR: merge the ascending real and imaginary
+// groups into one ascending row.
+template <typename S, typename C>
+__global__ void k_csr_fill_packed(int64_t n_rows, int log2C, const int64_t *chunk_ptr, const int32_t *chunk_len,
+                                  const int32_t *perm, const int32_t *col, const S *val, const int64_t *rowptr,
+                                  int32_t *ocol, C *oval) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    int64_t c = r >> log2C;
+    int64_t base = chunk_ptr[c] + (r & ((1 << log2C) - 1));
+    int64_t o = rowptr[perm ? perm[r] : r];
+    const int n_re = chunk_len[c] & 0xffff, n_im = chunk_len[c] >> 16;
+    int a = 0, b = n_re;
+    while (true) {
+        int32_t ca = a < n_re ? col[base + ((int64_t)a << log2C)] : -1;
+        int32_t cb = b < n_re + n_im ? col[base + ((int64_t)b << log2C)] : -1;
+        if (ca < 0 && cb < 0) break;
+        C z;
+        if (cb < 0 || (ca >= 0 && ca < cb)) {
+            z.x = val[base + ((int64_t)a << log2C)];
+            z.y = (S)0;
+            ocol[o] = ca;
+            ++a;
+        } else {
+            z.x = (S)0;
+            z.y = val[base + ((int64_t)b << log2C)];
+            ocol[o] = cb;
+            ++b;
+        }
+        oval[o] = z;
+        ++o;
+    }
+}
+
 cfd_status check_params(const cfd_topi_params *p, int C, int sigma, int prec) {
     if (!p) return fail(CFD_ERR_ARG, "params is NULL");
     int L[3] = {p->Nx, p->Ny, p->Nz};
@@ -250,32 +342,84 @@ cfd_status check_params(const cfd_topi_params *p, int C, int sigma, int prec) {
     return CFD_OK;
 }
 
-// Host replica of the chunk lengths (for sizes, no GPU work): after the
-// stable descending sort inside each window, chunk c's length is that of its
-// first row.
-int64_t host_slots(const Lattice &g, int C, int sigma) {
-    int64_t n_chunks = (g.n_rows + C - 1) / C;
+// Host replica of the chunk lengths (for sizes, no GPU work): rows sorted
+// stably by decreasing length inside each sigma window, then per chunk the
+// longest row (complex values) or the most real plus the most imaginary
+// entries (packed values).
+int64_t host_slots(const Lattice &g, int C, int sigma, bool packed) {
     int64_t slots = 0;
-    if (sigma == 1) {
-        for (int64_t c = 0; c < n_chunks; ++c) {
-            int mx = 0;
-            for (int64_t i = c * C; i < std::min<int64_t>((c + 1) * C, g.n_rows); ++i)
-                mx = std::max(mx, topi_row_len(i, g));
-            slots += (int64_t)mx * C;
+    std::vector<int64_t> order;
+    for (int64_t r0 = 0; r0 < g.n_rows; r0 += (sigma > 1 ? sigma : g.n_rows)) {
+        int64_t r1 = sigma > 1 ? std::min<int64_t>(r0 + sigma, g.n_rows) : g.n_rows;
+        order.clear();
+        if (sigma > 1) {
+            for (int k = TOPI_MAX_ROW; k >= 0; --k)
+                for (int64_t i = r0; i < r1; ++i)
+                    if (topi_row_len(i, g) == k) order.push_back(i);
         }
-        return slots;
-    }
-    std::vector<int> sorted;
-    for (int64_t r0 = 0; r0 < g.n_rows; r0 += sigma) {
-        int64_t r1 = std::min<int64_t>(r0 + sigma, g.n_rows);
-        int cnt[TOPI_MAX_ROW + 1] = {0};
-        for (int64_t i = r0; i < r1; ++i) ++cnt[topi_row_len(i, g)];
-        sorted.clear();
-        for (int k = TOPI_MAX_ROW; k >= 0; --k)
-            for (int q = 0; q < cnt[k]; ++q) sorted.push_back(k);
-        for (size_t a = 0; a < sorted.size(); a += C) slots += (int64_t)sorted[a] * C;
+        for (int64_t a = r0; a < r1; a += C) {
+            int mx = 0, mre = 0, mim = 0;
+            for (int64_t q = a; q < std::min<int64_t>(a + C, r1); ++q) {
+                int64_t i = sigma > 1 ? order[q - r0] : q;
+                mx = std::max(mx, topi_row_len(i, g));
+                int x, y;
+                topi_row_counts(i, g, &x, &y);
+                mre = std::max(mre, x);
+                mim = std::max(mim, y);
+            }
+            slots += (int64_t)(packed ? mre + mim : mx) * C;
+        }
     }
     return slots;
+}
+
+// After building realisation r into its slice of a batch with local indices:
+// shift chunk pointers by the slice's first slot, columns and the sorting
+// permutation by its first row, pad rows permute to themselves, and tag the
+// slice's chunks with r.
+__global__ void k_batch_fixup(int r, int64_t row_off, int64_t slot_off, int64_t n_chunks_r, int64_t n_rows_r,
+                              int64_t padded_r, int64_t slots_r, int64_t *chunk_ptr, int32_t *chunk_rid,
+                              int32_t *perm, int32_t *col) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < slots_r; e += stride)
+        if (col[e] >= 0) col[e] += (int32_t)row_off;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= n_chunks_r; e += stride) {
+        chunk_ptr[e] += slot_off;
+        if (e < n_chunks_r) chunk_rid[e] = r;
+    }
+    if (perm)
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < padded_r; e += stride)
+            perm[e] = (int32_t)(row_off + (e < n_rows_r ? perm[e] : e));
+}
+
+struct BatchLayout {
+    std::vector<int64_t> row_off, slot_off, slots, chunk_off;
+    int64_t nnz = 0, work = 0;
+};
+
+int64_t batch_pad(int C, int sigma) { return std::max<int64_t>(std::max(C, sigma), 32); }
+
+cfd_status batch_layout(const cfd_topi_params *p, int R, int C, int sigma, int prec, bool packed, BatchLayout &L) {
+    if (!p || R < 1) return fail(CFD_ERR_ARG, "empty batch");
+    const int64_t P = batch_pad(C, sigma);
+    L.row_off.assign(R + 1, 0);
+    L.slot_off.assign(R + 1, 0);
+    L.slots.assign(R, 0);
+    L.chunk_off.assign(R + 1, 0);
+    for (int r = 0; r < R; ++r) {
+        CFD_TRY(check_params(p + r, C, sigma, prec));
+        Lattice g = lattice_of(p + r);
+        int64_t padded = (g.n_rows + P - 1) / P * P;
+        L.row_off[r + 1] = L.row_off[r] + padded;
+        L.chunk_off[r + 1] = L.row_off[r + 1] / C;
+        L.slots[r] = host_slots(g, C, sigma, packed);
+        L.slot_off[r + 1] = L.slot_off[r] + L.slots[r];
+        for (int64_t i = 0; i < g.n_rows; i += 4) L.nnz += 4 * topi_row_len(i, g);
+        int64_t nch = padded / C;
+        L.work = std::max<int64_t>(L.work, (int64_t)(round_up((size_t)nch * 8, 256) + scan_workspace(nch)));
+    }
+    if (L.row_off[R] > 2147483647LL) return fail(CFD_ERR_ARG, "batch exceeds 32-bit column indices");
+    return CFD_OK;
 }
 
 }  // namespace
@@ -285,17 +429,19 @@ using namespace cfd;
 
 extern "C" {
 
-cfd_status cfd_matrix_query_size(const cfd_topi_params *p, int C, int sigma, int prec,
+cfd_status cfd_matrix_query_size(const cfd_topi_params *p, int C, int sigma, int prec_arg,
                                  cfd_matrix_sizes *out) {
     clear_error();
+    const bool packed = (prec_arg & CFD_PACK_RI) != 0;
+    const int prec = prec_arg & ~CFD_PACK_RI;
     CFD_TRY(check_params(p, C, sigma, prec));
     if (!out) return fail(CFD_ERR_ARG, "out is NULL");
     Lattice g = lattice_of(p);
     int64_t nnz = 0;
     for (int64_t i = 0; i < g.n_rows; i += 4) nnz += 4 * topi_row_len(i, g);
     int64_t n_chunks = (g.n_rows + C - 1) / C;
-    int64_t slots = host_slots(g, C, sigma);
-    size_t s = (prec == CFD_C128) ? 16 : 8;
+    int64_t slots = host_slots(g, C, sigma, packed);
+    size_t s = packed ? ((prec == CFD_C128) ? 8 : 4) : ((prec == CFD_C128) ? 16 : 8);
     out->n_rows = g.n_rows;
     out->nnz = nnz;
     out->n_chunks = n_chunks;
@@ -309,10 +455,12 @@ cfd_status cfd_matrix_query_size(const cfd_topi_params *p, int C, int sigma, int
     return CFD_OK;
 }
 
-cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec,
+cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec_arg,
                             const cfd_matrix_buffers *buf, cfd_matrix *out, cudaStream_t stream) {
     cfd_matrix_sizes sz;
-    CFD_TRY(cfd_matrix_query_size(p, C, sigma, prec, &sz));
+    CFD_TRY(cfd_matrix_query_size(p, C, sigma, prec_arg, &sz));
+    const bool packed = (prec_arg & CFD_PACK_RI) != 0;
+    const int prec = prec_arg & ~CFD_PACK_RI;
     if (!buf || !out) return fail(CFD_ERR_ARG, "buffers or out is NULL");
     if (!buf->val || !buf->col || !buf->chunk_ptr || !buf->chunk_len || !buf->work ||
         (sigma > 1 && !buf->perm))
@@ -334,14 +482,23 @@ cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec
     if (perm) {
         int64_t windows = (g.n_rows + sigma - 1) / sigma;
         k_sigma_sort<<<(unsigned)((windows + T - 1) / T), T, 0, stream>>>(g, sigma, perm);
+        CFD_COUNT_LAUNCH();
     }
-    k_chunk_len<<<(unsigned)((sz.n_chunks + T - 1) / T), T, 0, stream>>>(g, log2C, sz.n_chunks, perm,
+    k_chunk_len<<<(unsigned)((sz.n_chunks + T - 1) / T), T, 0, stream>>>(g, log2C, sz.n_chunks, perm, packed,
                                                                           chunk_len, slots);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     CFD_TRY(exclusive_scan_i64(slots, chunk_ptr, sz.n_chunks, scan_work, stream));
     int64_t rows_pad = sz.n_chunks << log2C;
     unsigned grid = (unsigned)((rows_pad + T - 1) / T);
-    if (prec == CFD_C128)
+    if (packed && prec == CFD_C128)
+        k_fill_packed<double><<<grid, T, 0, stream>>>(g, v, log2C, sz.n_chunks, perm, chunk_ptr, chunk_len,
+                                                      static_cast<int32_t *>(buf->col),
+                                                      static_cast<double *>(buf->val));
+    else if (packed)
+        k_fill_packed<float><<<grid, T, 0, stream>>>(g, v, log2C, sz.n_chunks, perm, chunk_ptr, chunk_len,
+                                                     static_cast<int32_t *>(buf->col), static_cast<float *>(buf->val));
+    else if (prec == CFD_C128)
         k_fill<double2><<<grid, T, 0, stream>>>(g, v, log2C, sz.n_chunks, perm, chunk_ptr, chunk_len,
                                                 static_cast<int32_t *>(buf->col),
                                                 static_cast<double2 *>(buf->val));
@@ -349,6 +506,7 @@ cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec
         k_fill<float2><<<grid, T, 0, stream>>>(g, v, log2C, sz.n_chunks, perm, chunk_ptr, chunk_len,
                                                static_cast<int32_t *>(buf->col),
                                                static_cast<float2 *>(buf->val));
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     out->n_rows = sz.n_rows;
     out->nnz = sz.nnz;
@@ -357,12 +515,114 @@ cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec
     out->C = C;
     out->sigma = sigma;
     out->prec = prec;
-    out->reserved = 0;
+    out->flags = ((prec_arg & CFD_PACK_RI) ? CFD_MATRIX_PACKED : 0) | (TOPI_MAX_ROW << CFD_MATRIX_SLOTS_SHIFT);
     out->val = buf->val;
     out->col = static_cast<int32_t *>(buf->col);
     out->chunk_ptr = chunk_ptr;
     out->chunk_len = chunk_len;
     out->perm = perm;
+    return CFD_OK;
+}
+
+cfd_status cfd_batch_query_size(const cfd_topi_params *p, int R, int C, int sigma, int prec_arg,
+                                cfd_matrix_sizes *out, int64_t *row_off) {
+    clear_error();
+    const bool packed = (prec_arg & CFD_PACK_RI) != 0;
+    const int prec = prec_arg & ~CFD_PACK_RI;
+    if (!out) return fail(CFD_ERR_ARG, "out is NULL");
+    BatchLayout L;
+    CFD_TRY(batch_layout(p, R, C, sigma, prec, packed, L));
+    size_t s = packed ? ((prec == CFD_C128) ? 8 : 4) : ((prec == CFD_C128) ? 16 : 8);
+    int64_t N = L.row_off[R], n_chunks = N / C, slots = L.slot_off[R];
+    out->n_rows = N;
+    out->nnz = L.nnz;
+    out->n_chunks = n_chunks;
+    out->n_slots = slots;
+    out->bytes_val = (int64_t)round_up((size_t)slots * s, 256);
+    out->bytes_col = (int64_t)round_up((size_t)slots * 4, 256);
+    out->bytes_chunk_ptr = (int64_t)round_up((size_t)(n_chunks + 1) * 8, 256);
+    out->bytes_chunk_len = (int64_t)round_up((size_t)n_chunks * 4, 256);
+    out->bytes_perm = sigma > 1 ? (int64_t)round_up((size_t)N * 4, 256) : 0;
+    out->bytes_work = L.work;
+    if (row_off)
+        for (int r = 0; r <= R; ++r) row_off[r] = L.row_off[r];
+    return CFD_OK;
+}
+
+cfd_status cfd_build_batch(const cfd_topi_params *p, int R, int C, int sigma, int prec_arg,
+                           const cfd_matrix_buffers *buf, int32_t *chunk_rid, cfd_matrix *out,
+                           cudaStream_t stream) {
+    clear_error();
+    cfd_matrix_sizes sz;
+    CFD_TRY(cfd_batch_query_size(p, R, C, sigma, prec_arg, &sz, nullptr));
+    const bool packed = (prec_arg & CFD_PACK_RI) != 0;
+    const int prec = prec_arg & ~CFD_PACK_RI;
+    if (!buf || !out || !chunk_rid) return fail(CFD_ERR_ARG, "buffers, chunk_rid or out is NULL");
+    if (!buf->val || !buf->col || !buf->chunk_ptr || !buf->chunk_len || !buf->work || (sigma > 1 && !buf->perm))
+        return fail(CFD_ERR_ARG, "a required matrix buffer is NULL");
+    if (!aligned16(buf->val) || !aligned16(buf->col) || !aligned16(buf->chunk_ptr) || !aligned16(buf->work))
+        return fail(CFD_ERR_ARG, "matrix buffers must be 16-byte aligned");
+    BatchLayout L;
+    CFD_TRY(batch_layout(p, R, C, sigma, prec, packed, L));
+    int log2C = 0;
+    while ((1 << log2C) < C) ++log2C;
+    int32_t *perm_all = sigma > 1 ? static_cast<int32_t *>(buf->perm) : nullptr;
+    int32_t *chunk_len = static_cast<int32_t *>(buf->chunk_len);
+    int64_t *chunk_ptr = static_cast<int64_t *>(buf->chunk_ptr);
+    int32_t *col = static_cast<int32_t *>(buf->col);
+    const int T = 256;
+    for (int r = 0; r < R; ++r) {
+        Lattice g = lattice_of(p + r);
+        TopiValues v{p[r].t, p[r].m, p[r].gamma, p[r].seed};
+        const int64_t padded = L.row_off[r + 1] - L.row_off[r];
+        const int64_t nch = padded / C, c0 = L.chunk_off[r], s0 = L.slot_off[r];
+        Carve w(buf->work, (size_t)sz.bytes_work);
+        int64_t *slots = w.take<int64_t>((size_t)nch);
+        void *scan_work = w.take<char>(scan_workspace(nch));
+        int32_t *perm = perm_all ? perm_all + L.row_off[r] : nullptr;
+        if (perm) {
+            int64_t windows = (g.n_rows + sigma - 1) / sigma;
+            k_sigma_sort<<<(unsigned)((windows + T - 1) / T), T, 0, stream>>>(g, sigma, perm);
+            CFD_COUNT_LAUNCH();
+        }
+        k_chunk_len<<<(unsigned)((nch + T - 1) / T), T, 0, stream>>>(g, log2C, nch, perm, packed, chunk_len + c0,
+                                                                     slots);
+        CFD_COUNT_LAUNCH();
+        CFD_LAUNCH_CHECK();
+        CFD_TRY(exclusive_scan_i64(slots, chunk_ptr + c0, nch, scan_work, stream));
+        unsigned grid = (unsigned)((padded + T - 1) / T);
+        if (packed && prec == CFD_C128)
+            k_fill_packed<double><<<grid, T, 0, stream>>>(g, v, log2C, nch, perm, chunk_ptr + c0, chunk_len + c0,
+                                                          col + s0, static_cast<double *>(buf->val) + s0);
+        else if (packed)
+            k_fill_packed<float><<<grid, T, 0, stream>>>(g, v, log2C, nch, perm, chunk_ptr + c0, chunk_len + c0,
+                                                         col + s0, static_cast<float *>(buf->val) + s0);
+        else if (prec == CFD_C128)
+            k_fill<double2><<<grid, T, 0, stream>>>(g, v, log2C, nch, perm, chunk_ptr + c0, chunk_len + c0, col + s0,
+                                                    static_cast<double2 *>(buf->val) + s0);
+        else
+            k_fill<float2><<<grid, T, 0, stream>>>(g, v, log2C, nch, perm, chunk_ptr + c0, chunk_len + c0, col + s0,
+                                                   static_cast<float2 *>(buf->val) + s0);
+        CFD_COUNT_LAUNCH();
+        int64_t span = std::max(std::max(L.slots[r], nch + 1), padded);
+        k_batch_fixup<<<(unsigned)std::min<int64_t>((span + T - 1) / T, 4096), T, 0, stream>>>(
+            r, L.row_off[r], s0, nch, g.n_rows, padded, L.slots[r], chunk_ptr + c0, chunk_rid + c0, perm, col + s0);
+        CFD_COUNT_LAUNCH();
+        CFD_LAUNCH_CHECK();
+    }
+    out->n_rows = sz.n_rows;
+    out->nnz = sz.nnz;
+    out->n_chunks = sz.n_chunks;
+    out->n_slots = sz.n_slots;
+    out->C = C;
+    out->sigma = sigma;
+    out->prec = prec;
+    out->flags = ((prec_arg & CFD_PACK_RI) ? CFD_MATRIX_PACKED : 0) | (TOPI_MAX_ROW << CFD_MATRIX_SLOTS_SHIFT);
+    out->val = buf->val;
+    out->col = col;
+    out->chunk_ptr = chunk_ptr;
+    out->chunk_len = chunk_len;
+    out->perm = perm_all;
     return CFD_OK;
 }
 
@@ -385,10 +645,21 @@ cfd_status cfd_matrix_export_csr(const cfd_matrix *H, int64_t *rowptr, int32_t *
     const int T = 256;
     unsigned grid = (unsigned)((H->n_rows + T - 1) / T);
     k_csr_len<<<grid, T, 0, stream>>>(H->n_rows, log2C, H->chunk_ptr, H->chunk_len, H->perm, H->col,
-                                      rowlen);
+                                      (H->flags & CFD_MATRIX_PACKED) != 0, rowlen);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     CFD_TRY(exclusive_scan_i64(rowlen, rowptr, H->n_rows, scan_work, stream));
-    if (H->prec == CFD_C128)
+    const bool packed = (H->flags & CFD_MATRIX_PACKED) != 0;
+    if (packed && H->prec == CFD_C128)
+        k_csr_fill_packed<double, double2><<<grid, T, 0, stream>>>(H->n_rows, log2C, H->chunk_ptr, H->chunk_len,
+                                                                   H->perm, H->col,
+                                                                   static_cast<const double *>(H->val), rowptr, col,
+                                                                   static_cast<double2 *>(val));
+    else if (packed)
+        k_csr_fill_packed<float, float2><<<grid, T, 0, stream>>>(H->n_rows, log2C, H->chunk_ptr, H->chunk_len,
+                                                                 H->perm, H->col, static_cast<const float *>(H->val),
+                                                                 rowptr, col, static_cast<float2 *>(val));
+    else if (H->prec == CFD_C128)
         k_csr_fill<double2><<<grid, T, 0, stream>>>(H->n_rows, log2C, H->chunk_ptr, H->chunk_len,
                                                     H->perm, H->col, static_cast<const double2 *>(H->val),
                                                     rowptr, col, static_cast<double2 *>(val));
@@ -396,6 +667,7 @@ cfd_status cfd_matrix_export_csr(const cfd_matrix *H, int64_t *rowptr, int32_t *
         k_csr_fill<float2><<<grid, T, 0, stream>>>(H->n_rows, log2C, H->chunk_ptr, H->chunk_len,
                                                    H->perm, H->col, static_cast<const float2 *>(H->val),
                                                    rowptr, col, static_cast<float2 *>(val));
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;
 }

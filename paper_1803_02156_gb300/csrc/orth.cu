@@ -72,9 +72,11 @@ cfd_status svqb_pass(double2 *X, int64_t ldx, int64_t N, int n, double tau, void
     if (!c.fits()) return fail(CFD_ERR_OOM, "orthogonalisation workspace too small");
     CFD_TRY(gram(X, ldx, n, X, ldx, n, N, S, n, gw, stream));
     k_svqb_scale<<<(n * n + 255) / 256, 256, 0, stream>>>(S, n, d);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     CFD_TRY(eigh(S + (size_t)n * n, n, n, theta, Q, n, ew, ew_bytes, stream, nullptr));
     k_svqb_coeff<<<(n * n + 255) / 256, 256, 0, stream>>>(Q, theta, d, n, tau, M, rank_dev ? rank_dev : rank);
+    CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     CFD_TRY(project_inplace(X, ldx, N, n, M, n, n, pw, stream));
     return CFD_OK;
@@ -177,7 +179,7 @@ cfd_status rayleigh_ritz_impl(const cfd_matrix *H, const cfd_block &X, double *e
     double2 *Y = c.take<double2>((size_t)n * n);
     double *partial = c.take<double>((size_t)STEP_MAX_GRID * 2 * 64);
     unsigned *ticket = c.take<unsigned>(64);
-    double *dots = c.take<double>(2 * 64);
+    (void)c.take<double>(2 * 64);
     double *gw = reinterpret_cast<double *>(c.take<char>(gram_workspace(N, n, n)));
     double *pw = reinterpret_cast<double *>(c.take<char>(project_workspace(n, n)));
     size_t ewb = eigh_workspace(n);
@@ -185,7 +187,7 @@ cfd_status rayleigh_ritz_impl(const cfd_matrix *H, const cfd_block &X, double *e
     double *rw = reinterpret_cast<double *>(c.take<char>(resid_workspace(n)));
     double2 *Xp = static_cast<double2 *>(X.ptr);
     CFD_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), stream));
-    CFD_TRY(spmmv_block(H, Xp, X.ld, Z, n, n, partial, ticket, dots, stream));
+    CFD_TRY(spmmv_block(H, Xp, X.ld, Z, n, n, partial, ticket, nullptr, stream));   // no moments needed
     CFD_TRY(gram(Xp, X.ld, n, Z, n, n, N, G, n, gw, stream));
     CFD_TRY(eigh(G, n, n, evals, Y, n, ew, ewb, stream, nullptr));
     CFD_TRY(project_inplace(Xp, X.ld, N, n, Y, n, n, pw, stream));

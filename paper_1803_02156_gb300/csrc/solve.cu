@@ -7,6 +7,7 @@
 
 #include "dense.cuh"
 #include "filter.cuh"
+#include "solve_rules.h"
 
 namespace cfd {
 
@@ -109,15 +110,15 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
 
     double *ev_dev = reinterpret_cast<double *>(static_cast<char *>(work) + 1024);   // n <= 256 doubles
     double *rs_dev = ev_dev + DENSE_MAX_COLS;
-    std::vector<int> hist, hist_low;
-    bool low = mixed;
+    ConvergenceTracker tr;
+    tr.start(p->n_t, mixed);
     const double switch_tol = p->switch_tol > 0 ? p->switch_tol : 1e-4;
     res->rank_min = n;
     for (int it = 1; it <= p->max_iter; ++it) {
         cudaEvent_t e0, e1, e2, e3;
         cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); cudaEventCreate(&e3);
         cudaEventRecord(e0, stream);
-        CFD_TRY(filter_impl(low ? H_low : H, lmin, lmax, p->lam_l, p->lam_r, p->n_p, X, p->n_b, 0, 0, scratch,
+        CFD_TRY(filter_impl(tr.low ? H_low : H, lmin, lmax, p->lam_l, p->lam_r, p->n_p, X, p->n_b, 0, 0, scratch,
                             scratch_bytes, nullptr, stream));
         cudaEventRecord(e1, stream);
         int rank = n;
@@ -129,7 +130,10 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
         CFD_CUDA(cudaMemcpyAsync(evals, ev_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaMemcpyAsync(resid, rs_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaMemcpyAsync(&rank, small + 8, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        int dev_status = 0;          // the filter workspace starts with its status word
+        CFD_CUDA(cudaMemcpyAsync(&dev_status, scratch, sizeof(int), cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaStreamSynchronize(stream));
+        if (dev_status == CFD_ERR_TIMEOUT) return fail(CFD_ERR_TIMEOUT, "a bounded device-side wait expired");
         float a = 0, b = 0, c = 0;
         cudaEventElapsedTime(&a, e0, e1);
         cudaEventElapsedTime(&b, e1, e2);
@@ -140,34 +144,23 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
         res->t_rr += c * 1e-3;
         res->rank_min = std::min(res->rank_min, rank);
         res->iters = it;
-        if (low) res->iters_low = it;
+        if (tr.low) res->iters_low = it;
 
         int cnt = 0, cnt_low = 0;
+        double mr = kNoPair, mrl = kNoPair;
         for (int j = 0; j < n; ++j) {
-            bool in = evals[j] >= p->lam_l && evals[j] <= p->lam_r;
-            if (in && resid[j] <= p->tol) ++cnt;
-            if (in && resid[j] <= switch_tol) ++cnt_low;
+            if (!(evals[j] >= p->lam_l && evals[j] <= p->lam_r)) continue;
+            if (resid[j] <= p->tol) ++cnt;
+            else mr = std::min(mr, resid[j]);
+            if (resid[j] <= switch_tol) ++cnt_low;
+            else mrl = std::min(mrl, resid[j]);
         }
         res->n_conv = cnt;
-        hist.push_back(cnt);
-        if (!low) {
-            size_t h = hist.size();
-            bool done = (p->n_t > 0 && cnt >= p->n_t) ||
-                        (h >= 3 && cnt >= 1 && hist[h - 1] == hist[h - 2] && hist[h - 2] == hist[h - 3]);
-            if (done) {
-                res->t_total = now_s() - t0;
-                return CFD_OK;
-            }
-        } else {
-            // switch to the fp64 filter once the fp32 filter has delivered the target
-            // count to switch_tol, or that count stopped growing
-            hist_low.push_back(cnt_low);
-            size_t h = hist_low.size();
-            if ((p->n_t > 0 && cnt_low >= p->n_t) || (h >= 2 && cnt_low >= 1 && hist_low[h - 1] <= hist_low[h - 2])) {
-                low = false;
-                hist.clear();
-            }
+        if (tr.update(cnt, cnt_low, mr, mrl)) {
+            res->t_total = now_s() - t0;
+            return CFD_OK;
         }
+        if (tr.low && tr.switch_ready) tr.leave_low();
     }
     res->t_total = now_s() - t0;
     return fail(CFD_ERR_NOCONV, "no convergence in %d iterations (%d converged)", p->max_iter, res->n_conv);

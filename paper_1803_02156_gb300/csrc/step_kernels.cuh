@@ -1,0 +1,707 @@
+// Fused ChebFD step kernels (templates).  Included by the four step_*.cu
+// translation units, each instantiating one (precision, value storage) pair.
+#pragma once
+
+#include <algorithm>
+#include <cooperative_groups.h>
+#include <type_traits>
+
+#include "filter.cuh"
+
+namespace cfd {
+
+namespace cg = cooperative_groups;
+
+__device__ __forceinline__ size_t round_up_dev(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------ step kernel --
+
+namespace {
+
+template <typename T> struct MomentAcc;
+
+// fp64 path: plain fp64 sums per thread.
+template <> struct MomentAcc<double> {
+    double s = 0.0;
+    // s += a b + c d as two fused multiply-adds (fp64 is the scarce pipe)
+    __device__ void add2(double a, double b, double c, double d) { s = fma(c, d, fma(a, b, s)); }
+    __device__ double value() const { return s; }
+};
+
+// fp32 path: compensated (Kahan) fp32 sums per thread, widened once at the end.
+template <> struct MomentAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ void add2(float a, float b, float c2, float d) {
+        float y = fma(a, b, c2 * d) - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ double value() const { return (double)s - (double)c; }
+};
+
+template <typename C, int VPT> struct Pack { C v[VPT]; };
+
+
+template <typename C, int VPT>
+__device__ __forceinline__ Pack<C, VPT> ld_nc(const C *p) {
+    Pack<C, VPT> r;
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) r.v[q] = __ldg(p + q);
+    return r;
+}
+
+template <>
+__device__ __forceinline__ Pack<float2, 2> ld_nc<float2, 2>(const float2 *p) {
+    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    Pack<float2, 2> r;
+    r.v[0] = make_float2(a.x, a.y);
+    r.v[1] = make_float2(a.z, a.w);
+    return r;
+}
+
+template <typename C, int VPT>
+__device__ __forceinline__ Pack<C, VPT> ld_rw(const C *p) {
+    Pack<C, VPT> r;
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) r.v[q] = p[q];
+    return r;
+}
+
+template <>
+__device__ __forceinline__ Pack<float2, 2> ld_rw<float2, 2>(const float2 *p) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    Pack<float2, 2> r;
+    r.v[0] = make_float2(a.x, a.y);
+    r.v[1] = make_float2(a.z, a.w);
+    return r;
+}
+
+template <typename C, int VPT>
+__device__ __forceinline__ void st(C *p, const Pack<C, VPT> &r) {
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) p[q] = r.v[q];
+}
+
+template <>
+__device__ __forceinline__ void st<float2, 2>(float2 *p, const Pack<float2, 2> &r) {
+    *reinterpret_cast<float4 *>(p) = make_float4(r.v[0].x, r.v[0].y, r.v[1].x, r.v[1].y);
+}
+
+}  // namespace
+
+
+// Load of one slot word: shared memory (staged chunks) or the read-only path.
+template <bool SMEM, typename V>
+__device__ __forceinline__ V ld_slot(const V *p) {
+    if constexpr (SMEM) return *p;
+    else return __ldg(p);
+}
+
+// Packed slots [k0, k1) of one row (slot k at colp[k << log2C]): each holds
+// one real scalar h; the group is real (h v added to acc) or imaginary
+// (i h v added: (-h vy, h vx)).  Padding slots (col -1, h 0) gather row 0 and
+// add zero.  U loads in flight.
+template <typename T, int VPT, bool IMAG, int U, bool SMEM>
+__device__ __forceinline__ void packed_group(const StepArgs<T> &A, const int32_t *colp, const T *valp, int log2C,
+                                             int k0, int k1, int j0, cplx_t<T> (&acc)[VPT]) {
+    using C = cplx_t<T>;
+    int k = k0;
+    for (; k + U <= k1; k += U) {
+        int cc[U];
+        T hv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cc[u] = max(ld_slot<SMEM>(colp + ((int64_t)(k + u) << log2C)), 0);
+            hv[u] = ld_slot<SMEM>(valp + ((int64_t)(k + u) << log2C));
+        }
+        Pack<C, VPT> vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) vv[u] = ld_nc<C, VPT>(A.vin + (int64_t)cc[u] * A.ldin + j0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < VPT; ++q) {
+                if (IMAG) {
+                    acc[q].x = fma(-hv[u], vv[u].v[q].y, acc[q].x);
+                    acc[q].y = fma(hv[u], vv[u].v[q].x, acc[q].y);
+                } else {
+                    acc[q].x = fma(hv[u], vv[u].v[q].x, acc[q].x);
+                    acc[q].y = fma(hv[u], vv[u].v[q].y, acc[q].y);
+                }
+            }
+    }
+    for (; k < k1; ++k) {
+        const int c = max(ld_slot<SMEM>(colp + ((int64_t)k << log2C)), 0);
+        const T h = ld_slot<SMEM>(valp + ((int64_t)k << log2C));
+        Pack<C, VPT> v = ld_nc<C, VPT>(A.vin + (int64_t)c * A.ldin + j0);
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            if (IMAG) {
+                acc[q].x = fma(-h, v.v[q].y, acc[q].x);
+                acc[q].y = fma(h, v.v[q].x, acc[q].y);
+            } else {
+                acc[q].x = fma(h, v.v[q].x, acc[q].x);
+                acc[q].y = fma(h, v.v[q].y, acc[q].y);
+            }
+        }
+    }
+}
+
+// Complex slots [0, len) of one row.
+template <typename T, int VPT, int U, bool SMEM>
+__device__ __forceinline__ void complex_slots(const StepArgs<T> &A, const int32_t *colp, const cplx_t<T> *valp,
+                                              int log2C, int len, int j0, cplx_t<T> (&acc)[VPT]) {
+    using C = cplx_t<T>;
+    int k = 0;
+    for (; k + U <= len; k += U) {
+        int cc[U];
+        C hh[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cc[u] = max(ld_slot<SMEM>(colp + ((int64_t)(k + u) << log2C)), 0);      // padding: col -1, value 0
+            hh[u] = ld_slot<SMEM>(valp + ((int64_t)(k + u) << log2C));
+        }
+        Pack<C, VPT> vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) vv[u] = ld_nc<C, VPT>(A.vin + (int64_t)cc[u] * A.ldin + j0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < VPT; ++q) cfma(acc[q], hh[u], vv[u].v[q]);
+    }
+    for (; k < len; ++k) {
+        const int c = max(ld_slot<SMEM>(colp + ((int64_t)k << log2C)), 0);
+        const C h = ld_slot<SMEM>(valp + ((int64_t)k << log2C));
+        Pack<C, VPT> v = ld_nc<C, VPT>(A.vin + (int64_t)c * A.ldin + j0);
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) cfma(acc[q], h, v.v[q]);
+    }
+}
+
+// Map and weights of one step for a row: the step's own, or in a batch
+// (A.chunk_rid set) those of the chunk's realisation.
+template <typename T, int KIND>
+struct StepCoef {
+    T a, beta, g0, g1, g2;
+    __device__ __forceinline__ void init(const StepArgs<T> &A) {
+        a = (T)A.a;
+        beta = (T)A.beta;
+        g0 = g1 = g2 = 0;
+        if (!A.chunk_rid) {
+            if (KIND == STEP_SECOND) {
+                g0 = (T)A.gc[0];
+                g1 = (T)A.gc[1];
+                g2 = (T)A.gc[2];
+            } else if (KIND == STEP_GENERAL) {
+                g0 = (T)A.gc[A.p];
+            }
+        }
+    }
+    __device__ __forceinline__ void for_chunk(const StepArgs<T> &A, int64_t ch) {
+        if (!A.chunk_rid) return;
+        const double *rc = A.rcoef + (int64_t)__ldg(A.chunk_rid + ch) * A.rcoef_ld;
+        a = (T)((KIND == STEP_FIRST ? 1.0 : 2.0) * __ldg(rc));
+        beta = (T)__ldg(rc + 1);
+        if (KIND == STEP_SECOND) {
+            g0 = (T)__ldg(rc + 2);
+            g1 = (T)__ldg(rc + 3);
+            g2 = (T)__ldg(rc + 4);
+        } else if (KIND == STEP_GENERAL) {
+            g0 = (T)__ldg(rc + 2 + A.p);
+        }
+    }
+};
+
+// One row i of a fused step: the row's slots (colp/valp, slot k at
+// k << log2C; nre real slots first when packed) gathered against V_cur, then
+// shift, scale, three-term recurrence, accumulation into X, moment dots.
+template <typename T, int NB, int VPT, int KIND, bool MOM, bool PACK, bool SMEM>
+__device__ __forceinline__ void process_row(const StepArgs<T> &A, int64_t i, const int32_t *colp, const void *valp,
+                                            int log2C, int nre, int len, int j0, const StepCoef<T, KIND> &cf,
+                                            MomentAcc<T> (&uu)[VPT], MomentAcc<T> (&wu)[VPT]) {
+    using C = cplx_t<T>;
+    constexpr int UNR = 4;
+    // operands of the epilogue do not depend on the gathers: issue their
+    // (streaming) loads first so their latency overlaps the SpMMV
+    const Pack<C, VPT> u = ld_nc<C, VPT>(A.vin + i * A.ldin + j0);
+    // A.x == nullptr: moments only (Algorithm 1 without line 12), X untouched;
+    // step 2 then needs the start block's row i, which is V_prev's role here
+    Pack<C, VPT> wo, xo;
+    if (KIND == STEP_GENERAL) wo = ld_rw<C, VPT>(A.w + i * A.ldw + j0);
+    if (KIND == STEP_SECOND) xo = ld_rw<C, VPT>(A.x ? A.x + i * A.ldx + j0 : A.x0 + i * A.ldx0 + j0);
+    if (KIND == STEP_GENERAL && A.x) xo = ld_rw<C, VPT>(A.x + i * A.ldx + j0);
+
+    C acc[VPT];
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) acc[q] = cmake<T>(0, 0);
+    if constexpr (PACK) {
+        packed_group<T, VPT, false, UNR, SMEM>(A, colp, static_cast<const T *>(valp), log2C, 0, nre, j0, acc);
+        packed_group<T, VPT, true, UNR, SMEM>(A, colp, static_cast<const T *>(valp), log2C, nre, len, j0, acc);
+    } else {
+        complex_slots<T, VPT, UNR, SMEM>(A, colp, static_cast<const C *>(valp), log2C, len, j0, acc);
+    }
+
+    const T a = cf.a, beta = cf.beta, g0 = cf.g0, g1 = cf.g1, g2 = cf.g2;
+    Pack<C, VPT> wn;
+    if (KIND == STEP_FIRST) {
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            wn.v[q].x = a * fma(-beta, u.v[q].x, acc[q].x);
+            wn.v[q].y = a * fma(-beta, u.v[q].y, acc[q].y);
+        }
+        st<C, VPT>(A.w + i * A.ldw + j0, wn);
+    } else if (KIND == STEP_SECOND) {
+        C *xp = A.x + i * A.ldx + j0;
+        Pack<C, VPT> xn;
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            wn.v[q].x = fma(a, fma(-beta, u.v[q].x, acc[q].x), -xo.v[q].x);
+            wn.v[q].y = fma(a, fma(-beta, u.v[q].y, acc[q].y), -xo.v[q].y);
+            xn.v[q].x = fma(g2, wn.v[q].x, fma(g1, u.v[q].x, g0 * xo.v[q].x));
+            xn.v[q].y = fma(g2, wn.v[q].y, fma(g1, u.v[q].y, g0 * xo.v[q].y));
+        }
+        st<C, VPT>(A.w + i * A.ldw + j0, wn);
+        if (A.x) st<C, VPT>(xp, xn);
+    } else {
+        C *wp = A.w + i * A.ldw + j0;
+        C *xp = A.x + i * A.ldx + j0;
+        Pack<C, VPT> xn;
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            wn.v[q].x = fma(a, fma(-beta, u.v[q].x, acc[q].x), -wo.v[q].x);
+            wn.v[q].y = fma(a, fma(-beta, u.v[q].y, acc[q].y), -wo.v[q].y);
+            xn.v[q].x = fma(g0, wn.v[q].x, xo.v[q].x);
+            xn.v[q].y = fma(g0, wn.v[q].y, xo.v[q].y);
+        }
+        st<C, VPT>(wp, wn);
+        if (A.x) st<C, VPT>(xp, xn);
+    }
+    if (MOM) {
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            uu[q].add2(u.v[q].x, u.v[q].x, u.v[q].y, u.v[q].y);
+            wu[q].add2(wn.v[q].x, u.v[q].x, wn.v[q].y, u.v[q].y);
+        }
+    }
+}
+
+// Rows of one fused ChebFD step for a block of NB vectors, accumulating the
+// thread's moment dot products.  Thread layout: a warp covers RPW = 32 / TPR
+// rows at a time, TPR = NB / VPT threads per row, each thread VPT
+// consecutive vectors of its row.  Each CTA sweeps whole SELL chunks (its
+// warps cover the chunk's C rows, RPW rows per warp at a time), so a chunk's
+// matrix lines are read by one SM; CTAs take chunks grid-stride, so at any
+// time the GPU works on a contiguous window of rows and the gathered rows of
+// V_cur stay in L2.
+template <typename T, int NB, int VPT, int KIND, bool MOM, bool PACK>
+__device__ __forceinline__ void step_rows(const StepArgs<T> &A, MomentAcc<T> (&uu)[VPT],
+                                          MomentAcc<T> (&wu)[VPT]) {
+    constexpr int TPR = NB / VPT;
+    constexpr int RPW = 32 / TPR;
+    static_assert(TPR >= 1 && TPR <= 32 && (32 % TPR) == 0, "bad thread split");
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int sub = lane / TPR;
+    const int j0 = (lane % TPR) * VPT;
+    const int log2C = A.H.log2C;
+    StepCoef<T, KIND> cf;
+    cf.init(A);
+
+    const int64_t n_rows = A.H.n_rows;
+    const int chunk_h = 1 << log2C;
+    const int64_t n_chunks = (n_rows + chunk_h - 1) >> log2C;
+    const int rows_per_pass = STEP_WARPS * RPW;
+    const int passes = (chunk_h + rows_per_pass - 1) / rows_per_pass;
+    const int64_t n_items = n_chunks * passes;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int64_t ch = item / passes;
+        const int rr = (int)(item % passes) * rows_per_pass + warp * RPW + sub;
+        if (rr >= chunk_h) continue;
+        const int64_t r = (ch << log2C) + rr;
+        if (r >= n_rows) continue;
+        const int64_t base = __ldg(A.H.chunk_ptr + ch) + rr;
+        const int cl = __ldg(A.H.chunk_len + ch);
+        // packed: cl holds the real (low 16 bits) and imaginary (high) slot counts
+        const int nre = PACK ? (cl & 0xffff) : cl;
+        const int len = PACK ? nre + (cl >> 16) : cl;
+        const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
+        cf.for_chunk(A, ch);
+        const void *valp = PACK ? (const void *)(A.H.pval + base) : (const void *)(A.H.val + base);
+        process_row<T, NB, VPT, KIND, MOM, PACK, false>(A, i, A.H.col + base, valp, log2C, nre, len, j0, cf, uu, wu);
+    }
+}
+
+// Deterministic reduction of the threads' moment sums: warps (shuffles), the
+// CTA (shared memory, fixed order), then across CTAs by the last CTA to finish
+// (ticket counter), each in a fixed order.
+template <typename T, int NB, int VPT>
+__device__ __forceinline__ void reduce_moments(const StepArgs<T> &A, MomentAcc<T> (&uu)[VPT],
+                                               MomentAcc<T> (&wu)[VPT]) {
+    constexpr int TPR = NB / VPT;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int sub = lane / TPR;
+    const int j0 = (lane % TPR) * VPT;
+    __shared__ double red[STEP_WARPS][NB][2];
+    __shared__ bool last_cta;
+    double s_uu[VPT], s_wu[VPT];
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) {
+        s_uu[q] = uu[q].value();
+        s_wu[q] = wu[q].value();
+#pragma unroll
+        for (int off = TPR; off < 32; off <<= 1) {
+            s_uu[q] += __shfl_xor_sync(0xffffffffu, s_uu[q], off);
+            s_wu[q] += __shfl_xor_sync(0xffffffffu, s_wu[q], off);
+        }
+    }
+    if (sub == 0) {
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            red[warp][j0 + q][0] = s_uu[q];
+            red[warp][j0 + q][1] = s_wu[q];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * NB; e += blockDim.x) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < STEP_WARPS; ++w) s += red[w][e >> 1][e & 1];
+        A.partial[(int64_t)blockIdx.x * 2 * NB + e] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_cta = (atomicAdd(A.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (last_cta) {
+        __threadfence();
+        for (int e = warp; e < 2 * NB; e += STEP_WARPS) {
+            double s = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(A.partial + (int64_t)b * 2 * NB + e);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) A.dots[e] = s;
+        }
+        if (threadIdx.x == 0) *A.ticket = 0u;
+    }
+}
+
+// One fused ChebFD step (the paper's chebfd_op) over all rows, with the
+// moments reduced deterministically when MOM.
+template <typename T, int NB, int VPT, int KIND, bool MOM, bool PACK>
+__global__ void __launch_bounds__(STEP_WARPS * 32)
+k_cheb_step(const StepArgs<T> A) {
+    MomentAcc<T> uu[VPT], wu[VPT];
+    step_rows<T, NB, VPT, KIND, MOM, PACK>(A, uu, wu);
+    if (MOM) reduce_moments<T, NB, VPT>(A, uu, wu);
+}
+
+// ------------------------------------------------- TMA-staged general step --
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of a barrier, giving up after `limit` cycles:
+// returns false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
+// 1-D bulk copy global -> shared memory (TMA), completing on `bar`.
+// Addresses 16-byte aligned, size a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// General step with the matrix staged through shared memory: each CTA takes
+// whole chunks grid-stride; one thread copies the next chunk's column indices
+// and values with two TMA bulk copies into the other half of a double buffer
+// while the CTA computes the current chunk from shared memory, so a row's
+// critical path holds only its V_cur gathers.  Slot counts of a chunk are
+// multiples of C >= 4, so every copy is 16-byte aligned and sized.  A wait
+// that expires (after ~2^32 cycles, about two seconds) records
+// CFD_ERR_TIMEOUT in *A.status and the CTA returns after draining its own
+// copies (bounded too).  A.staged == 2 is the test of that path: every
+// barrier expects 16 bytes more than are copied, so no wait can succeed, and
+// waits give up after 2^24 cycles.
+template <typename T, int NB, int VPT, bool MOM, bool PACK>
+__global__ void __launch_bounds__(STEP_WARPS * 32)
+k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
+    using C = cplx_t<T>;
+    using V = typename std::conditional<PACK, T, C>::type;
+    constexpr int TPR = NB / VPT;
+    constexpr int RPW = 32 / TPR;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_len[2];
+    const int col_bytes = (int)round_up_dev((size_t)slots_cap * 4, 16);
+    int32_t *col_s[2] = {reinterpret_cast<int32_t *>(smem_raw), reinterpret_cast<int32_t *>(smem_raw + col_bytes)};
+    V *val_s[2] = {reinterpret_cast<V *>(smem_raw + 2 * col_bytes),
+                   reinterpret_cast<V *>(smem_raw + 2 * col_bytes + (size_t)slots_cap * sizeof(V))};
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int sub = lane / TPR;
+    const int j0 = (lane % TPR) * VPT;
+    const int log2C = A.H.log2C;
+    const int chunk_h = 1 << log2C;
+    const int64_t n_rows = A.H.n_rows;
+    const int64_t n_chunks = (n_rows + chunk_h - 1) >> log2C;
+    const V *gval = PACK ? reinterpret_cast<const V *>(A.H.pval) : reinterpret_cast<const V *>(A.H.val);
+    const uint32_t tx_extra = A.staged == 2 ? 16u : 0u;
+    const long long limit = A.staged == 2 ? (1LL << 24) : (1LL << 32);
+    StepCoef<T, STEP_GENERAL> cf;
+    cf.init(A);
+    MomentAcc<T> uu[VPT], wu[VPT];
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int64_t c, int b) {     // thread 0: stage chunk c into buffer b
+        const int cl = __ldg(A.H.chunk_len + c);
+        const int len = PACK ? (cl & 0xffff) + (cl >> 16) : cl;
+        const int64_t base = __ldg(A.H.chunk_ptr + c);
+        const uint32_t nslot = (uint32_t)len << log2C;
+        s_len[b] = cl;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[b], nslot * (uint32_t)(4 + sizeof(V)) + tx_extra);
+        if (nslot) {
+            tma_load_1d(col_s[b], A.H.col + base, nslot * 4u, &bar[b]);
+            tma_load_1d(val_s[b], gval + base, nslot * (uint32_t)sizeof(V), &bar[b]);
+        }
+    };
+
+    int k = 0;
+    bool ok = true;
+    if (tid == 0 && (int64_t)blockIdx.x < n_chunks) issue(blockIdx.x, 0);
+    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++k) {
+        const int b = k & 1;
+        if (tid == 0 && c + gridDim.x < n_chunks) issue(c + gridDim.x, b ^ 1);
+        ok = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        const int cl = s_len[b];
+        const int nre = PACK ? (cl & 0xffff) : cl;
+        const int len = PACK ? nre + (cl >> 16) : cl;
+        cf.for_chunk(A, c);
+        for (int rr = warp * RPW + sub; rr < chunk_h; rr += STEP_WARPS * RPW) {
+            const int64_t r = (c << log2C) + rr;
+            if (r >= n_rows) continue;
+            const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
+            process_row<T, NB, VPT, STEP_GENERAL, MOM, PACK, true>(A, i, col_s[b] + rr, val_s[b] + rr, log2C, nre,
+                                                                   len, j0, cf, uu, wu);
+        }
+        __syncthreads();          // buffer b is refilled only after every thread read it
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(A.status, (int)CFD_ERR_TIMEOUT);
+            // drain this CTA's copies still in flight (bounded): the current
+            // chunk's and the prefetched one
+            const int b = k & 1;
+            mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);
+            mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1), limit);
+        }
+        return;
+    }
+    if (MOM) reduce_moments<T, NB, VPT>(A, uu, wu);
+}
+
+// All n_p steps of Algorithm 1 for one block in a single cooperative launch:
+// the grid synchronises between steps (every step reads V_cur rows that
+// other CTAs wrote in the previous step).  No moments.  The CTA count must
+// not exceed the co-resident capacity (cooperative launch checks it).
+template <typename T, int NB, int VPT, bool PACK>
+__global__ void __launch_bounds__(STEP_WARPS * 32, 3)
+k_cheb_persistent(const StepArgs<T> A0, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> *xb, int64_t ldx, int n_p) {
+    cg::grid_group grid = cg::this_grid();
+    MomentAcc<T> uu[VPT], wu[VPT];
+    StepArgs<T> A = A0;
+    const double alpha = A0.a;
+    // step 1: V1 = H~ X_b
+    A.vin = xb; A.ldin = ldx; A.w = va; A.ldw = NB; A.x = nullptr; A.ldx = 0; A.a = alpha; A.p = 1;
+    step_rows<T, NB, VPT, STEP_FIRST, false, PACK>(A, uu, wu);
+    grid.sync();
+    // step 2: V2 = 2 H~ V1 - X_b, X_b = gc0 X_b + gc1 V1 + gc2 V2
+    A.vin = va; A.ldin = NB; A.w = vb; A.ldw = NB; A.x = xb; A.ldx = ldx; A.a = 2.0 * alpha; A.p = 2;
+    step_rows<T, NB, VPT, STEP_SECOND, false, PACK>(A, uu, wu);
+    for (int p = 3; p <= n_p; ++p) {
+        grid.sync();
+        A.vin = (p & 1) ? vb : va;
+        A.w = (p & 1) ? va : vb;
+        A.p = p;
+        step_rows<T, NB, VPT, STEP_GENERAL, false, PACK>(A, uu, wu);
+    }
+}
+
+// --------------------------------------------------------- launching --
+
+namespace {
+
+template <typename T, int NB, int VPT, int KIND, bool MOM, bool PACK>
+cfd_status launch_one(const StepArgs<T> &A, int grid_cap, cudaStream_t stream) {
+    constexpr bool STAGEABLE = (KIND == STEP_GENERAL);
+    const bool staged = STAGEABLE && A.staged;
+    using V = typename std::conditional<PACK, T, cplx_t<T>>::type;
+    int slots_cap = 0;
+    size_t smem = 0;
+    if (staged) {
+        if (!A.status) return fail(CFD_ERR_INTERNAL, "staged step without a status word");
+        slots_cap = A.H.slots_bound << A.H.log2C;
+        if (slots_cap <= 0) return fail(CFD_ERR_ARG, "matrix has no slot bound; cannot stage");
+        smem = 2 * round_up((size_t)slots_cap * 4, 16) + 2 * (size_t)slots_cap * sizeof(V);
+        if (smem > 200 * 1024) return fail(CFD_ERR_ARG, "chunk too large to stage (%zu bytes)", smem);
+    }
+    auto kern = k_cheb_step<T, NB, VPT, KIND, MOM, PACK>;
+    auto skern = k_cheb_step_staged<T, NB, VPT, MOM, PACK>;
+    static int occ[64][2] = {{0}};
+    static size_t occ_smem[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    const int which = staged ? 1 : 0;
+    if (occ[dev][which] == 0 || (staged && occ_smem[dev] != smem)) {
+        int o = 0;
+        if (staged) {
+            CFD_CUDA(cudaFuncSetAttribute(skern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, skern, STEP_WARPS * 32, smem));
+            occ_smem[dev] = smem;
+        } else {
+            CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, STEP_WARPS * 32, 0));
+        }
+        occ[dev][which] = std::max(1, std::min(o, STEP_MAX_CTAS_PER_SM));
+    }
+    constexpr int RPW = 32 / (NB / VPT);
+    const int64_t C = 1LL << A.H.log2C;
+    const int64_t passes = (C + STEP_WARPS * RPW - 1) / (STEP_WARPS * RPW);
+    const int64_t n_chunks = (A.H.n_rows + C - 1) / C;
+    int64_t need = staged ? n_chunks : n_chunks * passes;     // work items
+    int64_t grid = std::min<int64_t>((int64_t)occ[dev][which] * sm_count(), need);
+    if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
+    grid = std::max<int64_t>(grid, 1);
+    if (staged) {
+        if constexpr (STAGEABLE) skern<<<(unsigned)grid, STEP_WARPS * 32, smem, stream>>>(A, slots_cap);
+    } else {
+        kern<<<(unsigned)grid, STEP_WARPS * 32, 0, stream>>>(A);
+    }
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    return CFD_OK;
+}
+
+template <typename T, int NB, int VPT, bool MOM, bool PACK>
+cfd_status launch_kind_mp(int kind, const StepArgs<T> &A, int grid_cap, cudaStream_t s) {
+    switch (kind) {
+    case STEP_FIRST: return launch_one<T, NB, VPT, STEP_FIRST, MOM, PACK>(A, grid_cap, s);
+    case STEP_SECOND: return launch_one<T, NB, VPT, STEP_SECOND, MOM, PACK>(A, grid_cap, s);
+    default: return launch_one<T, NB, VPT, STEP_GENERAL, MOM, PACK>(A, grid_cap, s);
+    }
+}
+
+// Moments are reduced only when the caller asks for the dot products.
+template <typename T, int NB, int VPT, bool PACK>
+cfd_status launch_kind(int kind, const StepArgs<T> &A, int grid_cap, cudaStream_t s) {
+    if (A.dots) return launch_kind_mp<T, NB, VPT, true, PACK>(kind, A, grid_cap, s);
+    return launch_kind_mp<T, NB, VPT, false, PACK>(kind, A, grid_cap, s);
+}
+
+}  // namespace
+
+template <typename T, bool PACK>
+cfd_status launch_step_p(int kind, int nb, int vpt, const StepArgs<T> &A, int grid_cap, cudaStream_t s) {
+#define CFD_CASE(NB_, VPT_) \
+    if (nb == NB_ && vpt == VPT_) return launch_kind<T, NB_, VPT_, PACK>(kind, A, grid_cap, s);
+    CFD_CASE(1, 1)
+    CFD_CASE(8, 1)
+    CFD_CASE(8, 2)
+    CFD_CASE(16, 1)
+    CFD_CASE(16, 2)
+    CFD_CASE(32, 1)
+    CFD_CASE(32, 2)
+    CFD_CASE(64, 2)
+#undef CFD_CASE
+    return fail(CFD_ERR_ARG, "unsupported block width n_b=%d with %d vectors per thread", nb, vpt);
+}
+
+
+namespace {
+
+template <typename T, int NB, int VPT, bool PACK>
+cfd_status launch_persistent_nbp(const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> *xb, int64_t ldx,
+                                 int n_p, int grid_cap, cudaStream_t stream) {
+    auto kern = k_cheb_persistent<T, NB, VPT, PACK>;
+    static int occ[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (occ[dev] == 0) {
+        int o = 0;
+        CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, STEP_WARPS * 32, 0));
+        occ[dev] = std::max(1, std::min(o, STEP_MAX_CTAS_PER_SM));
+    }
+    constexpr int RPW = 32 / (NB / VPT);
+    const int64_t C = 1LL << A.H.log2C;
+    const int64_t passes = (C + STEP_WARPS * RPW - 1) / (STEP_WARPS * RPW);
+    int64_t need = (A.H.n_rows + C - 1) / C * passes;       // work items (chunk passes)
+    int64_t grid = std::min<int64_t>((int64_t)occ[dev] * sm_count(), need);
+    if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
+    grid = std::max<int64_t>(grid, 1);
+    StepArgs<T> a = A;
+    void *args[] = {&a, &va, &vb, &xb, &ldx, &n_p};
+    CFD_CUDA(cudaLaunchCooperativeKernel((void *)kern, dim3((unsigned)grid), dim3(STEP_WARPS * 32), args, 0, stream));
+    CFD_COUNT_LAUNCH();
+    return CFD_OK;
+}
+
+}  // namespace
+
+template <typename T, bool PACK>
+cfd_status launch_persistent_p(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> *xb,
+                               int64_t ldx, int n_p, int grid_cap, cudaStream_t s) {
+#define CFD_PCASE(NB_, VPT_) \
+    if (nb == NB_ && vpt == VPT_) return launch_persistent_nbp<T, NB_, VPT_, PACK>(A, va, vb, xb, ldx, n_p, grid_cap, s);
+    CFD_PCASE(8, 1)
+    CFD_PCASE(8, 2)
+    CFD_PCASE(16, 1)
+    CFD_PCASE(16, 2)
+    CFD_PCASE(32, 1)
+    CFD_PCASE(32, 2)
+    CFD_PCASE(64, 2)
+#undef CFD_PCASE
+    return fail(CFD_ERR_ARG, "unsupported block width n_b=%d with %d vectors per thread", nb, vpt);
+}
+
+
+}  // namespace cfd

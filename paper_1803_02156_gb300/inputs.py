@@ -61,3 +61,17 @@ def batched_lattices(count, base_seed=1000):
         nz = 8 + int(d[2] % np.uint64(17))
         out.append((nx, ny, nz, base_seed + r))
     return out
+
+
+def gaussian_block_device(N, n_s, seed, dtype=None, device="cuda"):
+    """Complex Gaussian N x n_s block generated on the device with a seeded
+    torch generator (for blocks too large to build on the host); any row can
+    be read back as an input for the oracle."""
+    import torch
+    dtype = dtype or torch.complex128
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    real = torch.float64 if dtype == torch.complex128 else torch.float32
+    z = torch.randn(N, n_s, 2, generator=g, device=device, dtype=real) * (0.5 ** 0.5)
+    return torch.view_as_complex(z).contiguous()
+

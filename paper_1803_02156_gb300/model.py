@@ -39,9 +39,11 @@ def step_flops(N, nnz, n_b):
     return (8 * nnz + 42 * N) * n_b
 
 
-def step_fma_flops(N, nnz, n_b):
-    """Flops the multiply-add pipe executes for one fused step: (8 nnz + 20 N) n_b."""
-    return (8 * nnz + 20 * N) * n_b
+def step_fma_flops(N, nnz, n_b, packed=False):
+    """Flops the multiply-add pipe executes for one fused step: (8 nnz + 20 N) n_b
+    with complex matrix values; (4 nnz + 20 N) n_b when every value is stored as
+    one real-or-imaginary scalar (two fused multiply-adds per nonzero)."""
+    return ((4 if packed else 8) * nnz + 20 * N) * n_b
 
 
 def intensity(n_b, nnzr=13, prec="c128"):

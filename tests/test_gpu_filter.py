@@ -175,3 +175,86 @@ def test_filter_full_size_properties(b):
     assert np.all(np.abs(mu) <= mu[:, :1] * (1 + 1e-9))
     assert np.all(np.linalg.norm(outs[0], axis=0) ** 2 <= n0 * (1 + 1e-9))
     assert np.array_equal(outs[0], outs[1])
+
+
+# --------------------------------------------------- packed real/imaginary values --
+
+@pytest.mark.parametrize("L,per,C,sigma", [((8, 8, 8), (1, 1, 0), 32, 1), ((17, 23, 9), (1, 1, 0), 32, 64),
+                                           ((5, 4, 6), (0, 1, 0), 16, 32)])
+@pytest.mark.parametrize("prec", ["c128p", "c64p"])
+def test_packed_matrix_exports_oracle_csr(b, L, per, C, sigma, prec):
+    import torch
+    H = b.cfd_build_matrix(b.topi_params(*L, seed=17, periodic=per), C, sigma, prec)
+    assert H.packed
+    rowptr, col, val = b.cfd_matrix_export_csr(H)
+    torch.cuda.synchronize()
+    ref = oracle.topi_csr(*L, seed=17, periodic=per)
+    assert np.array_equal(rowptr.cpu().numpy(), ref.rowptr)
+    assert np.array_equal(col.cpu().numpy(), ref.col)
+    want = ref.val if prec == "c128p" else ref.val.astype(np.complex64)
+    assert np.array_equal(val.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("prec,n_b", [("c128", 32), ("c128", 64), ("c64", 32), ("c64", 16)])
+def test_packed_filter_equals_complex_storage(b, prec, n_b):
+    """Skipping the multiplications by exact zeros changes only the order of
+    the row sums (real group, then imaginary group): the filtered block and
+    the moments agree with the complex storage's to rounding."""
+    import torch
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    L = (12, 10, 7)
+    Hc = b.cfd_build_matrix(b.topi_params(*L), 32, 1, prec)
+    Hp = b.cfd_build_matrix(b.topi_params(*L), 32, 1, prec + "p")
+    X0 = torch.from_numpy(inputs.gaussian_block(Hc.N, 64, seed=8)).to(dt).cuda()
+    Xc, Xp = X0.clone(), X0.clone()
+    mc = b.cfd_filter(Hc, -8.6, 8.6, -0.6, 0.4, 70, Xc, n_b, moments=True)
+    mp = b.cfd_filter(Hp, -8.6, 8.6, -0.6, 0.4, 70, Xp, n_b, moments=True)
+    tol = 1e-12 if prec == "c128" else 70 * 13 * 2.0 ** -24
+    assert (torch.linalg.norm(Xc - Xp) / torch.linalg.norm(Xc)).item() < tol
+    assert (torch.max(torch.abs(mc - mp)) / torch.max(torch.abs(mc))).item() < tol
+
+
+def test_packed_filter_parity_small_config(b):
+    w = workloads.SMALL
+    import torch
+    H = b.cfd_build_matrix(b.topi_params(*w.lattice), 32, 1, "c128p")
+    ref = oracle.topi_csr(*w.lattice)
+    X = inputs.gaussian_block(ref.N, w.n_s, seed=2)
+    Xg = torch.from_numpy(X).cuda()
+    b.cfd_filter(H, -8.6, 8.6, -0.7, 0.7, w.n_p, Xg, 32)
+    Y, _ = oracle.chebfd_filter(ref, -8.6, 8.6, -0.7, 0.7, w.n_p, X, 32)
+    assert np.linalg.norm(Xg.cpu().numpy() - Y) / np.linalg.norm(Y) < TOL_C128
+
+
+def test_packed_solve_and_bounds(b):
+    """Lanczos bounds and the solve accept the packed matrix."""
+    import torch
+    Hc = oracle.topi_csr(8, 8, 8)
+    ev = np.linalg.eigvalsh(Hc.dense())
+    delta, k = oracle.window_from_dense(ev, 16)
+    H = b.cfd_build_matrix(b.topi_params(8, 8, 8), 32, 1, "c128p")
+    lo, hi = b.cfd_spectral_bounds(H, 40)
+    assert lo <= ev[0] and ev[-1] <= hi
+    X = torch.empty(2048, 32, dtype=torch.complex128, device="cuda")
+    th, rs, res = b.cfd_solve(H, X, -delta, delta, 200, 32, n_t=k)
+    inside = (th >= -delta) & (th <= delta) & (rs <= 1e-10)
+    assert np.max(np.abs(np.sort(th[inside]) - np.sort(ev[np.abs(ev) < delta]))) < 1e-10
+
+
+def test_kpm_moments_only(b):
+    """Moments without the accumulation (Algorithm 1 without line 12) equal the
+    filter's moments and the oracle's; the vectors are left unchanged."""
+    import torch
+    L = (9, 8, 6)
+    H = b.cfd_build_matrix(b.topi_params(*L), 32, 1, "c128p")
+    ref = oracle.topi_csr(*L)
+    R = inputs.gaussian_block(ref.N, 16, seed=31)
+    Rg = torch.from_numpy(R).cuda()
+    mu = b.cfd_kpm_moments(H, -8.6, 8.6, 120, Rg, 16).cpu().numpy()
+    assert np.array_equal(Rg.cpu().numpy(), R)
+    _, dots = oracle.chebfd_filter(ref, -8.6, 8.6, -0.5, 0.5, 120, R, 16)
+    muref = oracle.kpm_moments(dots)
+    assert np.max(np.abs(mu - muref)) / np.max(np.abs(muref)) < 1e-11
+    Hc = b.cfd_build_matrix(b.topi_params(*L), 32, 1, "c64p")
+    mu32 = b.cfd_kpm_moments(Hc, -8.6, 8.6, 120, Rg.to(torch.complex64), 16).cpu().numpy()
+    assert np.max(np.abs(mu32 - muref)) / np.max(np.abs(muref)) < 120 * 13 * 2.0 ** -24
