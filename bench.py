@@ -53,8 +53,12 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg (profiling runs)")
     ap.add_argument("--tte", action="store_true", help="also time cfd_solve to n_t eigenpairs, fp64 vs mixed")
-    ap.add_argument("--mode", default="filter", choices=["filter", "batch"],
-                    help="filter: the 64x64x32 iteration (default); batch: 64 uneven realisations, batched vs looped")
+    ap.add_argument("--mode", default="filter", choices=["filter", "batch", "fusion", "host"],
+                    help="filter: the 64x64x32 iteration (default); batch: 64 uneven realisations, batched vs "
+                         "looped; fusion: fused step vs separate SpMMV + BLAS-1 calls; host: search space in "
+                         "host memory vs in HBM, against n_p")
+    ap.add_argument("--host-lattice", default="64x64x32", help="host mode: lattice Nx x Ny x Nz")
+    ap.add_argument("--host-n-s", type=int, default=128, help="host mode: search space width")
     ap.add_argument("--realisations", type=int, default=workloads.BATCH_COUNT)
     ap.add_argument("--prec", default="c128", choices=["c128", "c64"], help="filter arithmetic")
     ap.add_argument("--storage", default="packed", choices=["packed", "complex"],
@@ -426,11 +430,15 @@ def run_batch(a):
     def batched_filter():
         b.cfd_filter_batched(Bl, wdev, n_p, X, n_b)
 
+    def persistent_filter():
+        b.cfd_filter_batched(Bl, wdev, n_p, X, n_b, persistent=1)
+
     def looped_filter():
         for r in range(R):
             b.cfd_filter(singles[r][1], *wins[r], n_p, Xs[r], n_b)
 
     tb = timed(batched_filter, a.steps)
+    tp = timed(persistent_filter, 1)
     tl = timed(looped_filter, a.steps)
     byts = sum(model.filter_bytes(s[0].N, s[0].nnz, n_s, n_b, n_p, "c64") for s in singles)
 
@@ -444,7 +452,7 @@ def run_batch(a):
     tsb = time.perf_counter() - t0
     conv_b = [int(x.n_conv) for x in res]
     t0 = time.perf_counter()
-    conv_l, diffs = [], []
+    conv_l, diffs, common = [], [], []
     for r in range(R):
         Y = torch.empty(singles[r][0].N, n_s, dtype=torch.complex128, device="cuda")
         th, rr, rres = b.cfd_solve(singles[r][0], Y, wins[r][2], wins[r][3], n_p, n_b, H_low=singles[r][1],
@@ -453,9 +461,12 @@ def run_batch(a):
         conv_l.append(int(rres.n_conv))
         cl = np.sort(th[(th >= wins[r][2]) & (th <= wins[r][3]) & (rr <= 1e-10)])
         cb = np.sort(ev[r][(ev[r] >= wins[r][2]) & (ev[r] <= wins[r][3]) & (rs[r] <= 1e-10)])
-        k = min(len(cl), len(cb))
-        if k:
-            diffs.append(float(np.max(np.abs(cl[:k] - cb[:k]))))
+        # each run may converge a few pairs beyond n_t the other did not reach:
+        # compare every looped eigenvalue with the nearest batched one
+        if len(cl) and len(cb):
+            d = np.abs(cl[:, None] - cb[None, :]).min(axis=1)
+            common.append(int((d < 1e-8).sum()))
+            diffs.append(float(d[d < 1e-8].max()) if (d < 1e-8).any() else None)
     torch.cuda.synchronize()
     tsl = time.perf_counter() - t0
     out = {"metric": "batched ChebFD: filter GB/s and time to eigenpairs, batched vs looped", "unit": "GB/s",
@@ -465,12 +476,136 @@ def run_batch(a):
                       "n_s": n_s, "n_p": n_p, "n_b": n_b, "n_t": n_t,
                       "lattices": [list(l[:3]) for l in lat]},
            "filter": {"batched_s": round(tb, 4), "looped_s": round(tl, 4), "speedup": round(tl / tb, 3),
+                      "persistent_s": round(tp, 4),
                       "batched_gbs": round(byts / tb / 1e9, 1), "looped_gbs": round(byts / tl / 1e9, 1)},
            "time_to_eigenpairs": {"batched_s": round(tsb, 3), "looped_s": round(tsl, 3),
                                   "speedup": round(tsl / tsb, 3), "iters_batched": max(x.iters for x in res),
+                                  "batched_phase_s": {"filter": round(res[0].t_filter, 3),
+                                                      "orthogonalize": round(res[0].t_orth, 3),
+                                                      "rayleigh_ritz": round(res[0].t_rr, 3)},
                                   "converged_batched": conv_b, "converged_looped": conv_l,
-                                  "max_eval_diff": max(diffs) if diffs else None, "tol": 1e-10}}
+                                  "common_pairs": common,
+                                  "max_eval_diff_common": max(x for x in diffs if x is not None) if any(
+                                      x is not None for x in diffs) else None, "tol": 1e-10}}
     print(json.dumps(out))
+
+
+def run_fusion(a):
+    """Fusion ablation on the 64x64x32 lattice (Sect. 4, Fig. 2): one n_b = 32
+    block of n_p steps (with moments) through the fused step and through the
+    chain of separate SpMMV and BLAS-1 kernels, complex128 and complex64
+    (packed values; complex64 fused with and without TMA staging).  Reports
+    ms per step, model GB/s of the fused step, and the chain's own traffic."""
+    import torch
+    from paper_1803_02156_gb300 import binding as b, inputs
+    torch.cuda.set_device(0)
+    w = WORKLOAD
+    n_b, n_p = a.n_b, min(a.n_p, 200)
+    p = b.topi_params(*w.lattice, t=w.t, m=w.m, gamma=w.gamma, seed=w.seed, periodic=w.periodic)
+    X0 = None
+    res = {}
+    for prec in ("c128", "c64"):
+        H = b.cfd_build_matrix(p, w.sell_C, w.sell_sigma, prec + "p")
+        N, nnz = H.N, H.nnz
+        if X0 is None:
+            X0 = torch.from_numpy(inputs.gaussian_block(N, n_b, seed=w.x_seed)).cuda()
+        X = X0.to(torch.complex128 if prec == "c128" else torch.complex64)
+        ws = max(b.cfd_filter_unfused_workspace(N, n_b, n_b, n_p, prec, prec),
+                 b.cfd_filter_workspace(N, n_b, n_b, n_p, prec, prec))
+        work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+        arms = {"fused": lambda: b.cfd_filter(H, *BOUNDS, -0.3, 0.3, n_p, X, n_b, moments=True, work=work),
+                "unfused": lambda: b.cfd_filter_unfused(H, *BOUNDS, -0.3, 0.3, n_p, X, n_b, moments=True,
+                                                        work=work)}
+        if prec == "c64":
+            arms["fused_unstaged"] = lambda: b.cfd_filter_ex(H, *BOUNDS, -0.3, 0.3, n_p, X, n_b, moments=True,
+                                                             work=work, staged=-1)
+        out = {}
+        for name, f in arms.items():
+            for _ in range(max(a.warmup, 1)):
+                X.copy_(X0)
+                f()
+            ts = []
+            for _ in range(max(a.steps, 1)):
+                X.copy_(X0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                f()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3 / n_p)
+            t = statistics.median(ts)
+            out[name] = {"ms_per_step": round(t * 1e3, 4),
+                         "model_gbs": round(model.step_bytes(N, nnz, n_b, prec) / t / 1e9, 1)}
+        out["unfused"]["own_traffic_gbs"] = round(model.unfused_step_bytes(N, nnz, n_b, prec) / (
+            out["unfused"]["ms_per_step"] * 1e-3) / 1e9, 1)
+        out["fusion_speedup"] = round(out["unfused"]["ms_per_step"] / out["fused"]["ms_per_step"], 3)
+        res[prec] = out
+        del work, H
+    print(json.dumps({"metric": "fused vs unfused ChebFD step", "unit": "ms/step", "n_gpus": 1,
+                      "steps": a.steps, "warmup": a.warmup, "data": "synthetic",
+                      "config": {"workload": "topi-64x64x32", "n_b": n_b, "n_p": n_p, "storage": "packed"},
+                      "results": res}))
+
+
+def run_host(a):
+    """Search space in host memory (Sect. 5's larger-than-fast-memory case):
+    the filter with X resident in HBM (cfd_filter) against X in page-locked
+    host memory streamed block by block over the chip-to-chip link
+    (cfd_filter_host), complex128 packed, for several n_p.  The host penalty
+    is (t_host - t_device) / t_device."""
+    import torch
+    from paper_1803_02156_gb300 import binding as b, inputs
+    torch.cuda.set_device(0)
+    w = WORKLOAD
+    L = tuple(int(v) for v in a.host_lattice.split("x"))
+    n_s, n_b = a.host_n_s, a.n_b
+    p = b.topi_params(*L, t=w.t, m=w.m, gamma=w.gamma, seed=w.seed, periodic=w.periodic)
+    H = b.cfd_build_matrix(p, w.sell_C, w.sell_sigma, "c128p")
+    N, nnz = H.N, H.nnz
+    Xh = torch.from_numpy(inputs.gaussian_block(N, n_s, seed=w.x_seed)).pin_memory()
+    X0 = Xh.clone()
+    n_ps = [2, 5, 10, 20, 50, 100]
+    ws = max(b.cfd_filter_host_workspace(N, n_s, n_b, max(n_ps), "c128", "c128"),
+             b.cfd_filter_workspace(N, n_s, n_b, max(n_ps), "c128", "c128"))
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n_p in n_ps:
+        dev = torch.empty(N, n_s, dtype=torch.complex128, device="cuda")
+
+        def run_dev():
+            b.cfd_filter(H, *BOUNDS, -0.3, 0.3, n_p, dev, n_b, work=work)
+
+        def run_host_():
+            b._check(b.lib().cfd_filter_host(H.ref(), BOUNDS[0], BOUNDS[1], -0.3, 0.3, n_p, b.block_of(Xh), n_b,
+                                             b._ptr(work), work.numel(), b._ptr(None), b._stream(stream)))
+        res = {}
+        for name, f, reset in (("device", run_dev, lambda: dev.copy_(X0, non_blocking=True)),
+                               ("host", run_host_, lambda: Xh.copy_(X0))):
+            ts = []
+            for r in range(a.warmup + a.steps):
+                reset()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                f()
+                e1.record()
+                torch.cuda.synchronize()
+                if r >= a.warmup:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+            res[name] = statistics.median(ts)
+        moved = 2 * N * n_s * 16
+        rows.append({"n_p": n_p, "device_s": round(res["device"], 5), "host_s": round(res["host"], 5),
+                     "penalty": round(res["host"] / res["device"] - 1.0, 4),
+                     "host_link_gbs_if_serial": round(moved / max(res["host"] - res["device"], 1e-9) / 1e9, 1),
+                     "filter_gbs_host": round(model.filter_bytes(N, nnz, n_s, n_b, n_p) / res["host"] / 1e9, 1)})
+        del dev
+    print(json.dumps({"metric": "filter time, search space in host memory vs HBM", "unit": "s", "n_gpus": 1,
+                      "steps": a.steps, "warmup": a.warmup, "data": "synthetic", "dtype": "c128",
+                      "config": {"workload": "topi-%s" % a.host_lattice, "N": N, "n_s": n_s, "n_b": n_b,
+                                 "host_bytes": N * n_s * 16, "storage": "packed", "pinned": True},
+                      "results": rows}))
 
 
 def main():
@@ -479,6 +614,10 @@ def main():
         run_reference(a)
     elif a.mode == "batch":
         run_batch(a)
+    elif a.mode == "fusion":
+        run_fusion(a)
+    elif a.mode == "host":
+        run_host(a)
     else:
         run_gpu(a)
 

@@ -217,7 +217,8 @@ typedef struct cfd_block {
 /*
  * Device scratch bytes cfd_filter needs for an N x n_s block filtered in
  * blocks of n_b vectors with degree n_p, matrix precision prec_H and block
- * precision prec_X.
+ * precision prec_X.  Flag bits above the low byte (CFD_PACK_RI) are ignored
+ * by this and the other workspace queries.  Returns 0 for invalid sizes.
  */
 size_t cfd_filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X);
 
@@ -269,6 +270,44 @@ typedef struct cfd_filter_opts {
 cfd_status cfd_filter_ex(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
                          int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
                          double *moments, const cfd_filter_opts *opts, cudaStream_t stream);
+
+/*
+ * The same filter as cfd_filter, computed by a chain of separate standard
+ * calls instead of the fused step (the "SpMMV + BLAS1" baseline of Sect. 4,
+ * Fig. 2): per recurrence step one SpMMV Y = H U into a third block, three
+ * axpby updates (W = 2 alpha Y - W, W -= 2 alpha beta U, X += g_p c_p W) and,
+ * when moments is non-NULL, two dot products, each a kernel of its own.
+ * It reads and writes 14 block vectors per step where the fused step moves 5;
+ * it exists to measure what the fusion saves.  Arguments, layout, precision
+ * pairs and errors as cfd_filter; the result agrees with cfd_filter to
+ * rounding (the operations are associated differently).  work:
+ * cfd_filter_unfused_workspace(...) bytes (cfd_filter's plus one N x n_b
+ * block and the dot partials).  Asynchronous.
+ */
+size_t cfd_filter_unfused_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X);
+cfd_status cfd_filter_unfused(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                              int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
+                              double *moments, cudaStream_t stream);
+
+/*
+ * cfd_filter for a search space X held in HOST memory (X.ptr a host pointer,
+ * page-locked for copy/compute overlap; pageable memory works but
+ * serialises).  Only two n_b-column blocks of X are on the device at a time
+ * (Sect. 5: the filter needs fast memory for the active block and the two
+ * recurrence blocks only), so n_s N is limited by host memory, not HBM.
+ * While block b is filtered on `stream`, an internal copy stream writes block
+ * b - 1 back and brings block b + 1 in (pitched 2-D copies of the column
+ * window); the filtered X and the moments equal cfd_filter's bit for bit.
+ * Asynchronous on `stream`: X must not be touched by the host until the
+ * stream has been synchronised.  work: cfd_filter_host_workspace(...) bytes
+ * of device memory (the filter workspace for one block plus two N x n_b
+ * staging blocks).  moments: device pointer or NULL, as for cfd_filter.
+ * Errors as cfd_filter; CFD_ERR_ARG if X.ptr is device or managed memory.
+ */
+size_t cfd_filter_host_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X);
+cfd_status cfd_filter_host(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                           int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
+                           double *moments, cudaStream_t stream);
 
 /*
  * Chebyshev moments only (the kernel polynomial method: Algorithm 1 without
@@ -336,9 +375,10 @@ size_t cfd_filter_batched_workspace(int64_t N, int R, int n_s, int n_b, int n_p,
  * the map alpha_r (H - beta_r) and the weights g_k c_k of its realisation r,
  * from windows (device, [R][4] doubles: lmin, lmax, lam_l, lam_r).  X is the
  * N_total x n_s block of all realisations (padding rows must be zero and stay
- * zero).  With opts->persistent (default when opts is NULL) each n_b block is
- * one cooperative launch running all n_p steps of all realisations, the grid
- * synchronising between steps; otherwise one launch per step.  Per
+ * zero).  One launch per step covers all realisations; with
+ * opts->persistent each n_b block is instead one cooperative launch running
+ * all n_p steps, the grid synchronising between steps (slower on GB300: the
+ * three step kinds in one kernel limit occupancy).  Per
  * realisation the result equals cfd_filter on that realisation alone, bit for
  * bit.  No moments.  Same precision rules as cfd_filter.  Asynchronous.
  */
@@ -533,8 +573,8 @@ size_t cfd_solve_batched_workspace(const cfd_matrix *H, int R, const cfd_solve_p
  * (lmin, lmax, lam_l, lam_r per realisation), n_t[R] (target counts, 0 =
  * unknown).  From p: n_s (<= 64), n_p, n_b, tol, max_iter, policy,
  * switch_tol, seed, start.  X: N_total x n_s complex double with ld = n_s
- * (padding rows are zeroed).  Each iteration is one batched filter (a
- * persistent launch per n_b block for all realisations), a batched SVQB
+ * (padding rows are zeroed).  Each iteration is one batched filter (one
+ * launch per step for all realisations), a batched SVQB
  * (twice) and a batched Rayleigh-Ritz.  Realisations stop counting once
  * converged; the mixed policy switches to the fp64 filter when every
  * realisation is ready.  Outputs (host): evals[R][n_s], resid[R][n_s],

@@ -113,6 +113,16 @@ _PROTOS = {
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                      ctypes.POINTER(cfd_filter_opts), ctypes.c_void_p]),
+    "cfd_filter_unfused_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                       ctypes.c_int, ctypes.c_int]),
+    "cfd_filter_unfused": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "cfd_filter_host_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_int, ctypes.c_int]),
+    "cfd_filter_host": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
     "cfd_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cfd_kpm_moments": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        cfd_block, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
@@ -341,6 +351,45 @@ def cfd_filter_ex(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, vpt=0, grid_cap=0, m
     return mu
 
 
+def cfd_filter_unfused_workspace(N, n_s, n_b, n_p, prec_H, prec_X):
+    return lib().cfd_filter_unfused_workspace(N, n_s, n_b, n_p, _prec(prec_H), _prec(prec_X))
+
+
+def cfd_filter_unfused(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=None, stream=None):
+    """The filter as a chain of separate SpMMV and BLAS-1 kernels (fusion
+    baseline); same arguments and result as cfd_filter."""
+    blk = block_of(X)
+    ws = cfd_filter_unfused_workspace(H.N, blk.n_cols, n_b, n_p, H.prec, blk.prec)
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, X.device)
+    mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=X.device) if moments else None
+    _check(lib().cfd_filter_unfused(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
+                                    _ptr(mu), _stream(stream)))
+    return mu
+
+
+def cfd_filter_host_workspace(N, n_s, n_b, n_p, prec_H, prec_X):
+    return lib().cfd_filter_host_workspace(N, n_s, n_b, n_p, _prec(prec_H), _prec(prec_X))
+
+
+def cfd_filter_host(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=None, stream=None,
+                    device="cuda"):
+    """cfd_filter for X in host memory (a CPU tensor, pinned for overlap); X is
+    filtered in place once the stream is synchronised (this call synchronises
+    it).  Returns the device moments when moments=True."""
+    if X.is_cuda:
+        raise ValueError("cfd_filter_host takes a host (CPU) tensor")
+    blk = block_of(X)
+    ws = cfd_filter_host_workspace(H.N, blk.n_cols, n_b, n_p, H.prec, blk.prec)
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, device)
+    mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=device) if moments else None
+    _check(lib().cfd_filter_host(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
+                                 _ptr(mu), _stream(stream)))
+    (stream or torch.cuda.current_stream()).synchronize()
+    return mu
+
+
 def cfd_workspace_status(work, stream=None):
     """Device status of a filter workspace (raises CfdError on a recorded timeout)."""
     _check(lib().cfd_workspace_status(_ptr(work), _stream(stream)))
@@ -413,7 +462,7 @@ def cfd_build_batch(params_list, C=32, sigma=1, prec="c128", device="cuda", stre
     return Batch(out, bufs, list(params_list), rid, off)
 
 
-def cfd_filter_batched(B, windows, n_p, X, n_b, persistent=1, vpt=0, work=None, stream=None):
+def cfd_filter_batched(B, windows, n_p, X, n_b, persistent=0, vpt=0, work=None, stream=None):
     """Filter every realisation of batch B at once; windows: float64 device tensor [R, 4]
     (lmin, lmax, lam_l, lam_r per realisation)."""
     blk = block_of(X)

@@ -1,7 +1,7 @@
 // ChebFD restart loop on a batch of independent realisations (block-diagonal
 // batch matrix from cfd_build_batch): every iteration runs the batched filter
-// (one persistent launch per n_b block for all realisations), a batched SVQB
-// and a batched Rayleigh-Ritz, each a handful of launches for the whole batch.
+// (one launch per step for all realisations), a batched SVQB and a batched
+// Rayleigh-Ritz, each a handful of launches for the whole batch.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -195,7 +195,7 @@ cfd_status cfd_solve_batched(const cfd_matrix *H, const cfd_matrix *H_low, const
         cudaEvent_t e[4];
         for (auto &x : e) cudaEventCreate(&x);
         cudaEventRecord(e[0], stream);
-        CFD_TRY(filter_batched_impl(low ? H_low : H, chunk_rid, R, d_win, p->n_p, X, p->n_b, 0, 1, big, ws.big,
+        CFD_TRY(filter_batched_impl(low ? H_low : H, chunk_rid, R, d_win, p->n_p, X, p->n_b, 0, 0, big, ws.big,
                                     stream));
         cudaEventRecord(e[1], stream);
         // SVQB twice (Stathopoulos & Wu), batched over realisations

@@ -435,7 +435,7 @@ cfd_status cfd_filter_coeffs(double lmin, double lmax, double lam_l, double lam_
 
 size_t cfd_filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X) {
     if (N < 1 || n_b < 1 || n_p < 2) return 0;
-    return filter_workspace(N, n_s, n_b, n_p, prec_H, prec_X);
+    return filter_workspace(N, n_s, n_b, n_p, prec_H & 0xff, prec_X & 0xff);
 }
 
 cfd_status cfd_filter(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
@@ -476,14 +476,14 @@ cfd_status cfd_workspace_status(const void *work, cudaStream_t stream) {
 
 size_t cfd_filter_batched_workspace(int64_t N, int R, int n_s, int n_b, int n_p, int prec_H, int prec_X) {
     if (N < 1 || R < 1 || n_b < 1 || n_p < 2) return 0;
-    return batched_workspace(N, R, n_s, n_b, n_p, prec_H, prec_X);
+    return batched_workspace(N, R, n_s, n_b, n_p, prec_H & 0xff, prec_X & 0xff);
 }
 
 cfd_status cfd_filter_batched(const cfd_matrix *H, const int32_t *chunk_rid, int R, const double *windows, int n_p,
                               cfd_block X, int n_b, void *work, size_t work_bytes, const cfd_filter_opts *opts,
                               cudaStream_t stream) {
     clear_error();
-    int vpt = opts ? opts->vpt : 0, pers = opts ? opts->persistent : 1;
+    int vpt = opts ? opts->vpt : 0, pers = opts ? opts->persistent : 0;
     return filter_batched_impl(H, chunk_rid, R, windows, n_p, X, n_b, vpt, pers, work, work_bytes, stream);
 }
 

@@ -1,0 +1,113 @@
+// ChebFD filter of a search space held in host memory (Algorithm 2's
+// subspace blocking taken one level further: Sect. 5 notes that only the
+// active n_b block and the two recurrence blocks need fast memory while the
+// filter runs, so the n_s-wide search space can live in slower, larger
+// memory).  On a Grace-Blackwell node the host memory sits behind the
+// chip-to-chip link; two device block buffers are used in turn: while block b
+// is filtered on the caller's stream, a copy stream writes block b - 1 back
+// and brings block b + 1 in.  Blocks are column windows of the row-major
+// host block, moved with pitched 2-D copies.
+
+#include <algorithm>
+
+#include "filter.cuh"
+
+namespace cfd {
+
+namespace {
+
+size_t host_filter_workspace(int64_t N, int n_b, int n_p, int prec_H, int prec_X) {
+    const size_t sX = prec_X == CFD_C128 ? 16 : 8;
+    return round_up(filter_workspace(N, n_b, n_b, n_p, prec_H, prec_X), 256) + 2 * round_up((size_t)N * n_b * sX, 256);
+}
+
+// Stream and events of one call, released on every return path (destruction
+// while work is pending is deferred by the runtime until that work is done).
+struct CopyPipe {
+    cudaStream_t copy = nullptr;
+    cudaEvent_t start = nullptr, in[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr}, out = nullptr;
+    ~CopyPipe() {
+        for (cudaEvent_t e : {start, in[0], in[1], done[0], done[1], out})
+            if (e) cudaEventDestroy(e);
+        if (copy) cudaStreamDestroy(copy);
+    }
+    cfd_status create() {
+        CFD_CUDA(cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
+        for (cudaEvent_t *e : {&start, &in[0], &in[1], &done[0], &done[1], &out})
+            CFD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        return CFD_OK;
+    }
+};
+
+}  // namespace
+
+}  // namespace cfd
+
+using namespace cfd;
+
+extern "C" size_t cfd_filter_host_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X) {
+    (void)n_s;
+    if (N < 1 || n_b < 1 || n_p < 2) return 0;
+    return host_filter_workspace(N, n_b, n_p, prec_H & 0xff, prec_X & 0xff);
+}
+
+extern "C" cfd_status cfd_filter_host(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                                      int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,
+                                      cudaStream_t stream) {
+    clear_error();
+    CFD_TRY(check_matrix(H));
+    CFD_TRY(validate_block(X, H->n_rows));
+    if (n_b != 8 && n_b != 16 && n_b != 32 && n_b != 64) return fail(CFD_ERR_ARG, "n_b=%d not in {8,16,32,64}", n_b);
+    if (X.n_cols % n_b) return fail(CFD_ERR_ARG, "n_b=%d does not divide n_s=%d", n_b, X.n_cols);
+    if (n_p < 2) return fail(CFD_ERR_ARG, "n_p=%d < 2", n_p);
+    if (!work) return fail(CFD_ERR_ARG, "work is NULL");
+    if (!aligned16(work)) return fail(CFD_ERR_ARG, "work must be 16-byte aligned");
+    cudaPointerAttributes pa;
+    CFD_CUDA(cudaPointerGetAttributes(&pa, X.ptr));
+    if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)
+        return fail(CFD_ERR_ARG, "X must be host memory (use cfd_filter for device blocks)");
+    const size_t need = host_filter_workspace(H->n_rows, n_b, n_p, H->prec, X.prec);
+    if (work_bytes < need) return fail(CFD_ERR_OOM, "host filter workspace %zu < %zu bytes", work_bytes, need);
+
+    const int64_t N = H->n_rows;
+    const size_t sX = X.prec == CFD_C128 ? 16 : 8;
+    const size_t fws = round_up(filter_workspace(N, n_b, n_b, n_p, H->prec, X.prec), 256);
+    char *dbuf[2] = {static_cast<char *>(work) + fws,
+                     static_cast<char *>(work) + fws + round_up((size_t)N * n_b * sX, 256)};
+    const size_t hpitch = (size_t)X.ld * sX, width = (size_t)n_b * sX;
+    const int n_blocks = X.n_cols / n_b;
+    char *host = static_cast<char *>(X.ptr);
+
+    CopyPipe cp;
+    CFD_TRY(cp.create());
+    // the copy stream starts after the work already queued on `stream`
+    CFD_CUDA(cudaEventRecord(cp.start, stream));
+    CFD_CUDA(cudaStreamWaitEvent(cp.copy, cp.start, 0));
+    auto bring_in = [&](int b) -> cfd_status {
+        CFD_CUDA(cudaMemcpy2DAsync(dbuf[b & 1], width, host + (size_t)b * width, hpitch, width, (size_t)N,
+                                   cudaMemcpyHostToDevice, cp.copy));
+        CFD_CUDA(cudaEventRecord(cp.in[b & 1], cp.copy));
+        return CFD_OK;
+    };
+    CFD_TRY(bring_in(0));
+    if (n_blocks > 1) CFD_TRY(bring_in(1));
+    for (int b = 0; b < n_blocks; ++b) {
+        CFD_CUDA(cudaStreamWaitEvent(stream, cp.in[b & 1], 0));
+        cfd_block D = X;
+        D.ptr = dbuf[b & 1];
+        D.ld = n_b;
+        D.n_cols = n_b;
+        CFD_TRY(filter_impl(H, lmin, lmax, lam_l, lam_r, n_p, D, n_b, 0, 0, work, fws,
+                            moments ? moments + (int64_t)b * n_b * 2 * n_p : nullptr, stream));
+        CFD_CUDA(cudaEventRecord(cp.done[b & 1], stream));
+        // write block b back, then reuse its buffer for block b + 2
+        CFD_CUDA(cudaStreamWaitEvent(cp.copy, cp.done[b & 1], 0));
+        CFD_CUDA(cudaMemcpy2DAsync(host + (size_t)b * width, hpitch, dbuf[b & 1], width, width, (size_t)N,
+                                   cudaMemcpyDeviceToHost, cp.copy));
+        if (b + 2 < n_blocks) CFD_TRY(bring_in(b + 2));
+    }
+    // later work on `stream` sees the whole search space written back
+    CFD_CUDA(cudaEventRecord(cp.out, cp.copy));
+    CFD_CUDA(cudaStreamWaitEvent(stream, cp.out, 0));
+    return CFD_OK;
+}

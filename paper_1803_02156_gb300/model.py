@@ -34,6 +34,15 @@ def step_read_write_bytes(N, nnz, n_b, prec="c128"):
     return nnz * (s + IDX_BYTES) + 3 * N * n_b * s, 2 * N * n_b * s
 
 
+def unfused_step_bytes(N, nnz, n_b, prec="c128", moments=True):
+    """Minimum DRAM bytes of one step computed by separate calls (SpMMV into a
+    third block Y, then W = 2 alpha Y - W, W -= 2 alpha beta U, X += g W, and
+    the dots <U, U>, <W, U>): the matrix plus 2 + 3 + 3 + 3 (+ 1 + 2) block
+    vectors, 14 with the moments against the fused step's 5."""
+    s = scalar_bytes(prec)
+    return nnz * (s + IDX_BYTES) + (14 if moments else 11) * N * n_b * s
+
+
 def step_flops(N, nnz, n_b):
     """Paper-convention flops of one fused step: (8 nnz + 42 N) n_b."""
     return (8 * nnz + 42 * N) * n_b

@@ -1,0 +1,71 @@
+"""GPU tests of the filter over a search space held in host memory: the
+blocks go through two device staging buffers, so the filtered block and the
+moments must equal the device-resident filter bit for bit."""
+import numpy as np
+import pytest
+
+from paper_1803_02156_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def b():
+    import torch
+    from paper_1803_02156_gb300 import build, binding
+    assert torch.cuda.is_available()
+    build.build()
+    binding.lib()
+    return binding
+
+
+@pytest.mark.parametrize("L,n_s,n_b,n_p,prec,pinned", [
+    ((16, 16, 8), 128, 32, 40, "c128p", True),     # 4 blocks
+    ((13, 7, 5), 48, 16, 25, "c128", True),        # 3 blocks, ragged rows
+    ((8, 8, 8), 32, 32, 60, "c128p", False),       # one block, pageable memory
+    ((12, 10, 7), 64, 16, 30, "c64p", True),       # mixed: complex64 matrix, complex128 blocks
+])
+def test_host_filter_equals_device_filter(b, L, n_s, n_b, n_p, prec, pinned):
+    import torch
+    H = b.cfd_build_matrix(b.topi_params(*L, seed=1), 32, 1, prec)
+    X = torch.from_numpy(inputs.gaussian_block(H.N, n_s, seed=2))
+    Xd = X.cuda()
+    mu_d = b.cfd_filter(H, -8.6, 8.6, -0.6, 0.4, n_p, Xd, n_b, moments=True)
+    Xh = X.clone().pin_memory() if pinned else X.clone()
+    mu_h = b.cfd_filter_host(H, -8.6, 8.6, -0.6, 0.4, n_p, Xh, n_b, moments=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(Xh.numpy(), Xd.cpu().numpy())
+    assert np.array_equal(mu_h.cpu().numpy(), mu_d.cpu().numpy())
+    assert not np.array_equal(Xh.numpy(), X.numpy())
+
+
+def test_host_filter_strided_host_block(b):
+    """A column window of a wider host array (ld > n_s) is filtered in place;
+    the other columns are untouched."""
+    import torch
+    H = b.cfd_build_matrix(b.topi_params(8, 8, 4, seed=1), 32, 1, "c128p")
+    big = torch.from_numpy(inputs.gaussian_block(H.N, 48, seed=3)).pin_memory()
+    ref = big.clone()
+    win = big[:, 8:40]
+    b.cfd_filter_host(H, -8.6, 8.6, -0.5, 0.5, 20, win, 16)
+    Xd = ref[:, 8:40].contiguous().cuda()
+    b.cfd_filter(H, -8.6, 8.6, -0.5, 0.5, 20, Xd, 16)
+    assert np.array_equal(big[:, 8:40].numpy(), Xd.cpu().numpy())
+    assert np.array_equal(big[:, :8].numpy(), ref[:, :8].numpy())
+    assert np.array_equal(big[:, 40:].numpy(), ref[:, 40:].numpy())
+
+
+def test_host_filter_rejects_device_block(b):
+    import torch
+    from paper_1803_02156_gb300.binding import CfdError, block_of, lib, _ptr, _stream
+    H = b.cfd_build_matrix(b.topi_params(4, 4, 4), 32, 1, "c128")
+    Xd = torch.zeros(H.N, 16, dtype=torch.complex128, device="cuda")
+    work = torch.empty(b.cfd_filter_host_workspace(H.N, 16, 16, 10, "c128", "c128"), dtype=torch.uint8,
+                       device="cuda")
+    st = lib().cfd_filter_host(H.ref(), -8.6, 8.6, -0.5, 0.5, 10, block_of(Xd), 16, _ptr(work), work.numel(),
+                               _ptr(None), _stream())
+    assert st == 1          # CFD_ERR_ARG
+    with pytest.raises(ValueError):
+        b.cfd_filter_host(H, -8.6, 8.6, -0.5, 0.5, 10, Xd, 16)
+    with pytest.raises(CfdError):
+        b.cfd_filter_host(H, -8.6, 8.6, -0.5, 0.5, 10, Xd.cpu(), 12)
