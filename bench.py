@@ -283,13 +283,14 @@ def run_gpu(a):
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GFLOPS, 1),
                 "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
                 "peak_source": "nominal FP64 FMA rate (152 SMs x 2/clk x 2.07 GHz)",
-                "kernel": "k_cheb_step<double,%d,%d,GENERAL,moments,%s>" % (n_b, 2 if n_b >= 16 else 1, a.storage),
+                "kernel": "k_cheb_step_staged<double,%d,%d,moments,%s>" % (n_b, 2 if n_b >= 16 else 1, a.storage),
                 "avg_launch_ms": round(1e3 * t_launch, 4), "hbm_gbs": round(gbs_launch, 1),
                 "hbm_frac": round(gbs_launch / hbm, 4)}
     else:
         roof = {"bound": "hbm", "achieved": round(gbs_launch, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(gbs_launch / hbm, 4), "traffic": None, "peak_source": hbm_src,
-                "kernel": "k_cheb_step<float,%d,2,GENERAL,moments,%s>" % (n_b, a.storage),
+                "kernel": "k_cheb_step_staged<float,%d,2,moments,%s%s>" % (
+                    n_b, a.storage, ",chunk height 32" if a.storage == "packed" else ""),
                 "avg_launch_ms": round(1e3 * t_launch, 4)}
 
     e2e = None

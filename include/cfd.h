@@ -258,10 +258,18 @@ typedef struct cfd_filter_opts {
     int32_t grid_cap;     /* upper bound on CTAs per step launch (0: one wave of resident CTAs) */
     int32_t persistent;   /* 1: all n_p steps of a block in one cooperative launch (no moments) */
     int32_t staged;       /* 1: general steps stage matrix chunks in shared memory by TMA bulk copies;
-                             -1: never; 0: default (staged for complex-float matrices);
+                             -1: never; 0: default (staged);
                              2: test of the bounded waits (no wait can succeed; the filter
                              records CFD_ERR_TIMEOUT, see cfd_workspace_status) */
-    int32_t reserved[4];
+    int32_t gather;       /* staged general steps of packed matrices: slots of a row whose gathers of
+                             V_cur are in flight together; 16 or 8: the first 16 (8) slots at once,
+                             the rest in groups of four; 4: groups of four; 0: the library's
+                             default.  Results do not depend on it. */
+    int32_t fixed_chunk;  /* staged steps of packed matrices with C = 32: 1 uses the kernel compiled
+                             for that chunk height (32-bit gather offsets, where they fit); -1 the
+                             generic kernel; 0 the default (compiled height for complex float,
+                             generic for complex double).  Results do not depend on it. */
+    int32_t reserved[2];
 } cfd_filter_opts;
 
 /* cfd_filter with explicit kernel options (the autotuner's knobs besides n_b,

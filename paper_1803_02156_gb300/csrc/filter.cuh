@@ -10,6 +10,7 @@ namespace cfd {
 constexpr int STEP_WARPS = 8;             // warps per CTA
 constexpr int STEP_MAX_CTAS_PER_SM = 8;   // cap on resident CTAs per SM
 constexpr int STEP_MAX_GRID = 4096;       // cap on CTAs of one step launch
+constexpr int STEP_GATHER_ALL = 16;       // slots whose gathers a row issues at once (gather option)
 
 enum StepKind : int {
     STEP_FIRST = 0,    // w = a (H vin - beta vin)                 (Algorithm 1, line 4)
@@ -46,6 +47,12 @@ struct StepArgs {
     // status receives CFD_ERR_TIMEOUT if one of its bounded waits expires
     int staged = 0;
     int *status = nullptr;
+    // gathers in flight per row in staged general steps of packed matrices:
+    // STEP_GATHER_ALL (all of the first 16 slots at once) or groups of four
+    int gather = 0;
+    // staged packed steps of C = 32 matrices: the kernel compiled for that
+    // chunk height (>= 0) or the generic one (< 0); results are the same
+    int fixed_chunk = 0;
 };
 
 template <typename T>
@@ -67,6 +74,8 @@ struct FilterPlan {
     int n_b = 0, n_p = 0, vpt = 0, grid_cap = 0;
     bool persistent = false;
     int staged = 0;
+    int gather = 0;
+    int fixed_chunk = 0;
     double alpha = 0, beta = 0;
     const int32_t *chunk_rid = nullptr;   // batch: chunk -> realisation
     const double *rcoef = nullptr;        // batch: per realisation {alpha, beta, weights}
@@ -83,6 +92,7 @@ struct FilterScratch {
 
 // Whether the general steps default to the TMA-staged kernel for a matrix precision.
 bool default_staged(int prec);
+int default_gather(int prec);
 
 int default_vpt(int prec, int n_b);
 size_t filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X);
@@ -98,7 +108,8 @@ cfd_status launch_widen(const float2 *src, int64_t lds, double2 *dst, int64_t ld
 // The whole filter with all options (persistent: one cooperative launch per block).
 cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
                             const cfd_block &X, int n_b, int vpt, int grid_cap, int persistent, int staged,
-                            void *work, size_t work_bytes, double *moments, cudaStream_t stream);
+                            void *work, size_t work_bytes, double *moments, cudaStream_t stream, int gather = 0,
+                            int fixed_chunk = 0);
 size_t batched_workspace(int64_t N, int R, int n_s, int n_b, int n_p, int prec_H, int prec_X);
 cfd_status kpm_impl(const cfd_matrix *H, double lmin, double lmax, int n_p, const cfd_block &R, int n_b,
                     void *work, size_t work_bytes, double *moments, cudaStream_t stream);

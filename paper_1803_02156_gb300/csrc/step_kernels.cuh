@@ -148,6 +148,109 @@ __device__ __forceinline__ void packed_group(const StepArgs<T> &A, const int32_t
     }
 }
 
+// Packed slots [0, len) of one row with every gather of the first KMAX
+// slots in flight at once: indices and values are read (from shared memory
+// when staged), all gathers issued, then the multiply-adds run in slot order
+// (real group, then imaginary group: the order of packed_group, so the sums
+// are bitwise the same).  Slots beyond KMAX go through packed_group.  The
+// slot counts are uniform over a chunk, so the guards do not diverge.
+template <typename T, int VPT, int KMAX, bool SMEM>
+__device__ __forceinline__ void packed_all(const StepArgs<T> &A, const int32_t *colp, const T *valp, int log2C,
+                                           int nre, int len, int j0, cplx_t<T> (&acc)[VPT]) {
+    using C = cplx_t<T>;
+    const int kk = min(len, KMAX);
+    Pack<C, VPT> vv[KMAX];
+    // staged: the values are read again from shared memory after the
+    // gathers (no registers held across them); else kept from the first read
+    T hv[SMEM ? 1 : KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < kk) {
+            const int c = max(ld_slot<SMEM>(colp + ((int64_t)k << log2C)), 0);
+            if constexpr (!SMEM) hv[k] = ld_slot<SMEM>(valp + ((int64_t)k << log2C));
+            vv[k] = ld_nc<C, VPT>(A.vin + (int64_t)c * A.ldin + j0);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < kk) {
+            const T h = SMEM ? ld_slot<SMEM>(valp + ((int64_t)k << log2C)) : hv[SMEM ? 0 : k];
+#pragma unroll
+            for (int q = 0; q < VPT; ++q) {
+                if (k < nre) {
+                    acc[q].x = fma(h, vv[k].v[q].x, acc[q].x);
+                    acc[q].y = fma(h, vv[k].v[q].y, acc[q].y);
+                } else {
+                    acc[q].x = fma(-h, vv[k].v[q].y, acc[q].x);
+                    acc[q].y = fma(h, vv[k].v[q].x, acc[q].y);
+                }
+            }
+        }
+    }
+    if (len > KMAX) {
+        const int r1 = max(nre, KMAX);
+        packed_group<T, VPT, false, 4, SMEM>(A, colp, valp, log2C, KMAX, r1, j0, acc);
+        packed_group<T, VPT, true, 4, SMEM>(A, colp, valp, log2C, r1, len, j0, acc);
+    }
+}
+
+// Packed slots [0, len) of one staged row with the chunk height CH fixed at
+// compile time: slot k of the row sits at shared offset k * CH (immediate
+// offsets), and row c of V_cur at byte offset (c * ld16) * 16 from the
+// thread's base vbase (ld16 = the row stride in 16-byte units; the host
+// checks that n_rows * ld16 fits in 32 bits), so a gather costs one 32-bit
+// multiply and one wide multiply-add instead of 64-bit index arithmetic.
+// Same products in the same order as packed_group / packed_all: KMAX > 0
+// issues the first KMAX slots' gathers together, else groups of U.
+template <typename T, int VPT, int U, int KMAX, int CH>
+__device__ __forceinline__ void packed_row_fixed(const char *vbase, uint32_t ld16, const int32_t *colp,
+                                                 const T *valp, int nre, int len, cplx_t<T> (&acc)[VPT]) {
+    using C = cplx_t<T>;
+    auto gather = [&](int k) {
+        const uint32_t c = (uint32_t)max(colp[k * CH], 0);
+        return ld_nc<C, VPT>(reinterpret_cast<const C *>(vbase + (uint64_t)(c * ld16) * 16u));
+    };
+    auto madd = [&](int k, bool imag, const Pack<C, VPT> &v) {
+        const T h = valp[k * CH];
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            if (imag) {
+                acc[q].x = fma(-h, v.v[q].y, acc[q].x);
+                acc[q].y = fma(h, v.v[q].x, acc[q].y);
+            } else {
+                acc[q].x = fma(h, v.v[q].x, acc[q].x);
+                acc[q].y = fma(h, v.v[q].y, acc[q].y);
+            }
+        }
+    };
+    int k0 = 0;
+    if constexpr (KMAX > 0) {
+        const int kk = min(len, KMAX);
+        Pack<C, VPT> vv[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < kk) vv[k] = gather(k);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < kk) madd(k, k >= nre, vv[k]);
+        k0 = kk;
+    }
+    // the rest (all of the row when KMAX == 0): real group, then imaginary
+    for (int g = 0; g < 2; ++g) {
+        const bool imag = g == 1;
+        int k = imag ? max(k0, nre) : k0;
+        const int k1 = imag ? len : nre;
+        for (; k + U <= k1; k += U) {
+            Pack<C, VPT> vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) vv[u] = gather(k + u);
+#pragma unroll
+            for (int u = 0; u < U; ++u) madd(k + u, imag, vv[u]);
+        }
+        for (; k < k1; ++k) madd(k, imag, gather(k));
+    }
+}
+
 // Complex slots [0, len) of one row.
 template <typename T, int VPT, int U, bool SMEM>
 __device__ __forceinline__ void complex_slots(const StepArgs<T> &A, const int32_t *colp, const cplx_t<T> *valp,
@@ -216,7 +319,10 @@ struct StepCoef {
 // One row i of a fused step: the row's slots (colp/valp, slot k at
 // k << log2C; nre real slots first when packed) gathered against V_cur, then
 // shift, scale, three-term recurrence, accumulation into X, moment dots.
-template <typename T, int NB, int VPT, int KIND, bool MOM, bool PACK, bool SMEM>
+// KMAX > 0 (packed values): the first KMAX slots' gathers all in flight at
+// once (packed_all); 0: groups of four.  CH > 0 (staged packed rows): chunk
+// height fixed at compile time, 32-bit gather offsets (packed_row_fixed).
+template <typename T, int NB, int VPT, int KIND, bool MOM, bool PACK, bool SMEM, int KMAX = 0, int CH = 0>
 __device__ __forceinline__ void process_row(const StepArgs<T> &A, int64_t i, const int32_t *colp, const void *valp,
                                             int log2C, int nre, int len, int j0, const StepCoef<T, KIND> &cf,
                                             MomentAcc<T> (&uu)[VPT], MomentAcc<T> (&wu)[VPT]) {
@@ -235,7 +341,13 @@ __device__ __forceinline__ void process_row(const StepArgs<T> &A, int64_t i, con
     C acc[VPT];
 #pragma unroll
     for (int q = 0; q < VPT; ++q) acc[q] = cmake<T>(0, 0);
-    if constexpr (PACK) {
+    if constexpr (PACK && CH > 0) {
+        const uint32_t ld16 = (uint32_t)((A.ldin * (int64_t)sizeof(C)) >> 4);
+        packed_row_fixed<T, VPT, UNR, KMAX, CH>(reinterpret_cast<const char *>(A.vin + j0), ld16, colp,
+                                                static_cast<const T *>(valp), nre, len, acc);
+    } else if constexpr (PACK && KMAX > 0) {
+        packed_all<T, VPT, KMAX, SMEM>(A, colp, static_cast<const T *>(valp), log2C, nre, len, j0, acc);
+    } else if constexpr (PACK) {
         packed_group<T, VPT, false, UNR, SMEM>(A, colp, static_cast<const T *>(valp), log2C, 0, nre, j0, acc);
         packed_group<T, VPT, true, UNR, SMEM>(A, colp, static_cast<const T *>(valp), log2C, nre, len, j0, acc);
     } else {
@@ -451,8 +563,12 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
 // copies (bounded too).  A.staged == 2 is the test of that path: every
 // barrier expects 16 bytes more than are copied, so no wait can succeed, and
 // waits give up after 2^24 cycles.
-template <typename T, int NB, int VPT, bool MOM, bool PACK>
-__global__ void __launch_bounds__(STEP_WARPS * 32)
+// KMAX > 0: every gather of a row's first KMAX slots in flight at once
+// (packed values; registers capped so that two CTAs fit on an SM).  CH > 0:
+// the matrix's chunk height, fixed at compile time (packed values; the
+// host launches it only for C == CH and 32-bit gather offsets).
+template <typename T, int NB, int VPT, bool MOM, bool PACK, int KMAX = 0, int CH = 0>
+__global__ void __launch_bounds__(STEP_WARPS * 32, KMAX > 0 ? 2 : 0)
 k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
     using C = cplx_t<T>;
     using V = typename std::conditional<PACK, T, C>::type;
@@ -462,15 +578,17 @@ k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_len[2];
     const int col_bytes = (int)round_up_dev((size_t)slots_cap * 4, 16);
-    int32_t *col_s[2] = {reinterpret_cast<int32_t *>(smem_raw), reinterpret_cast<int32_t *>(smem_raw + col_bytes)};
-    V *val_s[2] = {reinterpret_cast<V *>(smem_raw + 2 * col_bytes),
-                   reinterpret_cast<V *>(smem_raw + 2 * col_bytes + (size_t)slots_cap * sizeof(V))};
+    // buffer b: indices at smem_raw + b col_bytes, values after both index buffers
+    auto col_s = [&](int b) { return reinterpret_cast<int32_t *>(smem_raw + b * col_bytes); };
+    auto val_s = [&](int b) {
+        return reinterpret_cast<V *>(smem_raw + 2 * col_bytes + (size_t)b * slots_cap * sizeof(V));
+    };
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int sub = lane / TPR;
     const int j0 = (lane % TPR) * VPT;
-    const int log2C = A.H.log2C;
-    const int chunk_h = 1 << log2C;
+    const int log2C = CH > 0 ? __ffs(CH) - 1 : A.H.log2C;
+    const int chunk_h = CH > 0 ? CH : 1 << log2C;
     const int64_t n_rows = A.H.n_rows;
     const int64_t n_chunks = (n_rows + chunk_h - 1) >> log2C;
     const V *gval = PACK ? reinterpret_cast<const V *>(A.H.pval) : reinterpret_cast<const V *>(A.H.val);
@@ -496,34 +614,40 @@ k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bar[b], nslot * (uint32_t)(4 + sizeof(V)) + tx_extra);
         if (nslot) {
-            tma_load_1d(col_s[b], A.H.col + base, nslot * 4u, &bar[b]);
-            tma_load_1d(val_s[b], gval + base, nslot * (uint32_t)sizeof(V), &bar[b]);
+            tma_load_1d(col_s(b), A.H.col + base, nslot * 4u, &bar[b]);
+            tma_load_1d(val_s(b), gval + base, nslot * (uint32_t)sizeof(V), &bar[b]);
         }
     };
 
     int k = 0;
     bool ok = true;
     if (tid == 0 && (int64_t)blockIdx.x < n_chunks) issue(blockIdx.x, 0);
+    __syncthreads();              // s_len[0] written by thread 0
     for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++k) {
         const int b = k & 1;
         if (tid == 0 && c + gridDim.x < n_chunks) issue(c + gridDim.x, b ^ 1);
-        ok = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);
-        if (!__syncthreads_and(ok)) {
+        // every thread waits for the chunk's copies itself; a thread whose
+        // wait expired skips the chunk, and the barrier below then stops all
+        const bool landed = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);
+        if (landed) {
+            const int cl = s_len[b];
+            const int nre = PACK ? (cl & 0xffff) : cl;
+            const int len = PACK ? nre + (cl >> 16) : cl;
+            cf.for_chunk(A, c);
+            for (int rr = warp * RPW + sub; rr < chunk_h; rr += STEP_WARPS * RPW) {
+                const int64_t r = (c << log2C) + rr;
+                if (r >= n_rows) continue;
+                const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
+                process_row<T, NB, VPT, STEP_GENERAL, MOM, PACK, true, KMAX, CH>(A, i, col_s(b) + rr, val_s(b) + rr,
+                                                                                 log2C, nre, len, j0, cf, uu, wu);
+            }
+        }
+        // one barrier per chunk: buffer b is refilled only after every thread
+        // read it, and an expired wait anywhere ends the sweep
+        if (!__syncthreads_and(landed)) {
             ok = false;
             break;
         }
-        const int cl = s_len[b];
-        const int nre = PACK ? (cl & 0xffff) : cl;
-        const int len = PACK ? nre + (cl >> 16) : cl;
-        cf.for_chunk(A, c);
-        for (int rr = warp * RPW + sub; rr < chunk_h; rr += STEP_WARPS * RPW) {
-            const int64_t r = (c << log2C) + rr;
-            if (r >= n_rows) continue;
-            const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
-            process_row<T, NB, VPT, STEP_GENERAL, MOM, PACK, true>(A, i, col_s[b] + rr, val_s[b] + rr, log2C, nre,
-                                                                   len, j0, cf, uu, wu);
-        }
-        __syncthreads();          // buffer b is refilled only after every thread read it
     }
     if (!ok) {
         if (tid == 0) {
@@ -585,19 +709,44 @@ cfd_status launch_one(const StepArgs<T> &A, int grid_cap, cudaStream_t stream) {
         if (smem > 200 * 1024) return fail(CFD_ERR_ARG, "chunk too large to stage (%zu bytes)", smem);
     }
     auto kern = k_cheb_step<T, NB, VPT, KIND, MOM, PACK>;
+    // staged general steps of packed matrices: the first 16 (or 8) slots'
+    // gathers of a row in flight at once, else groups of four
+    const int kmax = (staged && PACK) ? (A.gather >= STEP_GATHER_ALL ? STEP_GATHER_ALL : (A.gather >= 8 ? 8 : 0)) : 0;
+    // chunk height 32 compiled in, with 32-bit gather offsets (fits when
+    // every gathered row's offset in 16-byte units stays below 2^32); by
+    // default for fp32 only: the fp64 variant needs more registers, which
+    // costs a resident CTA on the FP64-bound step
+    const bool want_fixed = A.fixed_chunk > 0 || (A.fixed_chunk == 0 && sizeof(T) == 4);
+    const bool fixed = staged && PACK && want_fixed && A.H.log2C == 5 &&
+                       (uint64_t)A.H.n_rows * (uint64_t)((A.ldin * (int64_t)sizeof(cplx_t<T>)) >> 4) < (1ULL << 32);
     auto skern = k_cheb_step_staged<T, NB, VPT, MOM, PACK>;
-    static int occ[64][2] = {{0}};
-    static size_t occ_smem[64] = {0};
+    if constexpr (PACK && STAGEABLE) {
+        if (kmax == STEP_GATHER_ALL)
+            skern = fixed ? k_cheb_step_staged<T, NB, VPT, MOM, PACK, STEP_GATHER_ALL, 32>
+                          : k_cheb_step_staged<T, NB, VPT, MOM, PACK, STEP_GATHER_ALL>;
+        else if (kmax == 8)
+            skern = k_cheb_step_staged<T, NB, VPT, MOM, PACK, 8>;
+        else if (fixed)
+            skern = k_cheb_step_staged<T, NB, VPT, MOM, PACK, 0, 32>;
+    }
+    // occupancy cache per device and kernel variant: 0 plain; staged generic
+    // 1 (groups of four), 2 (8 at once), 3 (16 at once); staged fixed 4, 5 (16 at once)
+    static int occ[64][6] = {{0}};
+    static size_t occ_smem[64][6] = {{0}};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    const int which = staged ? 1 : 0;
-    if (occ[dev][which] == 0 || (staged && occ_smem[dev] != smem)) {
+    int which = 0;
+    if (staged) {
+        if (fixed && kmax != 8) which = kmax == STEP_GATHER_ALL ? 5 : 4;
+        else which = kmax == STEP_GATHER_ALL ? 3 : (kmax == 8 ? 2 : 1);
+    }
+    if (occ[dev][which] == 0 || (staged && occ_smem[dev][which] != smem)) {
         int o = 0;
         if (staged) {
             CFD_CUDA(cudaFuncSetAttribute(skern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, skern, STEP_WARPS * 32, smem));
-            occ_smem[dev] = smem;
+            occ_smem[dev][which] = smem;
         } else {
             CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, STEP_WARPS * 32, 0));
         }

@@ -258,3 +258,95 @@ def test_kpm_moments_only(b):
     Hc = b.cfd_build_matrix(b.topi_params(*L), 32, 1, "c64p")
     mu32 = b.cfd_kpm_moments(Hc, -8.6, 8.6, 120, Rg.to(torch.complex64), 16).cpu().numpy()
     assert np.max(np.abs(mu32 - muref)) / np.max(np.abs(muref)) < 120 * 13 * 2.0 ** -24
+
+
+# ------------------------------------------ gathers in flight (staged steps) --
+
+@pytest.mark.parametrize("prec,n_b", [("c64", 32), ("c64", 16), ("c64", 64), ("c128", 32)])
+@pytest.mark.parametrize("gather", [8, 16])
+def test_gather_all_equals_grouped(b, prec, n_b, gather):
+    """Staged general steps that issue all of a row's gathers at once (the
+    first 8 or 16 slots, the rest in groups of four) add the same products in
+    the same order as groups of four: the filtered block is bitwise equal.
+    The open-z lattice has interior chunks of 9 real + 4 imaginary slots and
+    boundary chunks of 8 + 3, so gather=8 runs both remainder branches.
+    Moments differ only in the order of the cross-CTA reduction."""
+    import torch
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    L = (8, 6, 5)
+    H = b.cfd_build_matrix(b.topi_params(*L), 32, 1, prec + "p")
+    X0 = torch.from_numpy(inputs.gaussian_block(H.N, 64, seed=9)).to(dt).cuda()
+    Xa, Xb = X0.clone(), X0.clone()
+    ma = b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, 40, Xa, n_b, staged=1, gather=4, moments=True)
+    mb = b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, 40, Xb, n_b, staged=1, gather=gather, moments=True)
+    torch.cuda.synchronize()
+    assert torch.equal(Xa, Xb)
+    tol = 1e-13 if prec == "c128" else 1e-5
+    assert (torch.max(torch.abs(ma - mb)) / torch.max(torch.abs(ma))).item() < tol
+
+
+def test_gather_all_c64_parity_small_config(b):
+    """The complex64 filter with all gathers in flight against the fp64 oracle
+    on the 8x8x8 configuration (n_p = 200), at the fp32 bound."""
+    import torch
+    w = workloads.SMALL
+    H = b.cfd_build_matrix(b.topi_params(*w.lattice), 32, 1, "c64p")
+    ref = oracle.topi_csr(*w.lattice)
+    X = inputs.gaussian_block(ref.N, w.n_s, seed=2)
+    Xg = torch.from_numpy(X).to(torch.complex64).cuda()
+    mu = b.cfd_filter_ex(H, -8.6, 8.6, -0.7, 0.7, w.n_p, Xg, 32, staged=1, gather=16, moments=True)
+    torch.cuda.synchronize()
+    Y, dots = oracle.chebfd_filter(ref, -8.6, 8.6, -0.7, 0.7, w.n_p, X, 32)
+    err = np.linalg.norm(Xg.cpu().numpy().astype(np.complex128) - Y) / np.linalg.norm(Y)
+    muref = oracle.kpm_moments(dots)
+    merr = np.max(np.abs(mu.cpu().numpy() - muref)) / np.max(np.abs(muref))
+    assert err < TOL_C64_200 and merr < TOL_C64_200, (err, merr)
+
+
+def test_gather_option_rejected(b):
+    import torch
+    H = b.cfd_build_matrix(b.topi_params(4, 4, 4), 32, 1, "c64p")
+    X = torch.zeros(H.N, 16, dtype=torch.complex64, device="cuda")
+    with pytest.raises(RuntimeError, match="gather"):
+        b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, 10, X, 16, gather=5)
+
+
+@pytest.mark.parametrize("prec,n_b,gather", [("c64", 32, 4), ("c64", 16, 16), ("c64", 64, 4), ("c128", 32, 4),
+                                             ("c128", 16, 4)])
+def test_fixed_chunk_kernel_equals_generic(b, prec, n_b, gather):
+    """The staged step compiled for chunk height 32 (immediate shared-memory
+    offsets, 32-bit gather offsets) adds the same products in the same order
+    as the generic staged step: bitwise equal filtered block, moments equal up
+    to the order of the cross-CTA reduction."""
+    import torch
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    L = (8, 6, 5)
+    H = b.cfd_build_matrix(b.topi_params(*L), 32, 1, prec + "p")
+    X0 = torch.from_numpy(inputs.gaussian_block(H.N, 64, seed=10)).to(dt).cuda()
+    Xa, Xb = X0.clone(), X0.clone()
+    ma = b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, 40, Xa, n_b, staged=1, gather=gather, fixed_chunk=-1,
+                         moments=True)
+    mb = b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, 40, Xb, n_b, staged=1, gather=gather, fixed_chunk=1,
+                         moments=True)
+    torch.cuda.synchronize()
+    assert torch.equal(Xa, Xb)
+    tol = 1e-13 if prec == "c128" else 1e-5
+    assert (torch.max(torch.abs(ma - mb)) / torch.max(torch.abs(ma))).item() < tol
+
+
+def test_fixed_chunk_kernel_parity_ragged(b):
+    """Chunk height 32 with a ragged last chunk (N = 4 * 13 * 7 * 5 = 1820
+    rows, not a multiple of 32) and sigma-sorted rows, complex128 staged,
+    against the oracle."""
+    import torch
+    L, n_s, n_b, n_p = (13, 7, 5), 32, 16, 30
+    H = b.cfd_build_matrix(b.topi_params(*L), 32, 64, "c128p")
+    ref = oracle.topi_csr(*L)
+    X = inputs.gaussian_block(ref.N, n_s, seed=2)
+    Xg = torch.from_numpy(X).cuda()
+    mu = b.cfd_filter_ex(H, -8.6, 8.6, -1.1, 0.4, n_p, Xg, n_b, staged=1, moments=True)
+    torch.cuda.synchronize()
+    Y, dots = oracle.chebfd_filter(ref, -8.6, 8.6, -1.1, 0.4, n_p, X, n_b)
+    assert np.linalg.norm(Xg.cpu().numpy() - Y) / np.linalg.norm(Y) < TOL_C128
+    muref = oracle.kpm_moments(dots)
+    assert np.max(np.abs(mu.cpu().numpy() - muref)) / np.max(np.abs(muref)) < TOL_C128
