@@ -53,10 +53,15 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg (profiling runs)")
     ap.add_argument("--tte", action="store_true", help="also time cfd_solve to n_t eigenpairs, fp64 vs mixed")
-    ap.add_argument("--mode", default="filter", choices=["filter", "batch", "fusion", "host"],
+    ap.add_argument("--tte-workload", default=None, choices=sorted(workloads.ALL),
+                    help="tte mode: the workload whose time to eigenpairs is measured (default: the 64x64x32 one)")
+    ap.add_argument("--mode", default="filter", choices=["filter", "batch", "fusion", "host", "sweep", "tte"],
                     help="filter: the 64x64x32 iteration (default); batch: 64 uneven realisations, batched vs "
                          "looped; fusion: fused step vs separate SpMMV + BLAS-1 calls; host: search space in "
-                         "host memory vs in HBM, against n_p")
+                         "host memory vs in HBM, against n_p; sweep: fused-filter throughput on the 64x64x32 "
+                         "lattice for n_b = 8..64, the 200x200x100 lattice (complex128) and the 128x128x64 "
+                         "lattice (complex64 filter on a complex128 block); tte: time to eigenpairs, fp64 vs "
+                         "mixed policy, on --tte-workload")
     ap.add_argument("--host-lattice", default="64x64x32", help="host mode: lattice Nx x Ny x Nz")
     ap.add_argument("--host-n-s", type=int, default=128, help="host mode: search space width")
     ap.add_argument("--realisations", type=int, default=workloads.BATCH_COUNT)
@@ -609,6 +614,88 @@ def run_host(a):
                       "results": rows}))
 
 
+def run_sweep(a):
+    """Fused-filter throughput (filter with moments, per-step CUDA-event time of
+    whole filter applications) on the configurations of the paper's method:
+    64x64x32 complex128 with n_b = 8, 16, 32, 64 (n_s = 128); 200x200x100
+    complex128 (N = 16e6, n_s = 256 in blocks of 32); 128x128x64 with the
+    complex64 filter on a complex128 block (n_s = 256).  Start blocks are
+    drawn on the device (seeded torch generator; the largest block is 65 GB).
+    GB/s by the minimum-traffic model, Gflop/s by the paper's count and by
+    the FP64/FP32 pipe's."""
+    import torch
+    from paper_1803_02156_gb300 import binding as b
+    torch.cuda.set_device(0)
+    hbm, hbm_src = measured_hbm_gbs()
+    rows = []
+    cases = [((64, 64, 32), "c128", "c128", 128, nb, 100) for nb in (8, 16, 32, 64)]
+    cases += [((200, 200, 100), "c128", "c128", 256, 32, 40), ((128, 128, 64), "c64", "c128", 256, 32, 50)]
+    for lat, ph, px, n_s, n_b, n_p in cases:
+        p = b.topi_params(*lat, t=WORKLOAD.t, m=WORKLOAD.m, gamma=WORKLOAD.gamma, seed=WORKLOAD.seed,
+                          periodic=WORKLOAD.periodic)
+        H = b.cfd_build_matrix(p, 32, 1, ph + "p")
+        g = torch.Generator(device="cuda")
+        g.manual_seed(WORKLOAD.x_seed)
+        dt = torch.complex128 if px == "c128" else torch.complex64
+        X = torch.randn(H.N, n_s, dtype=dt, device="cuda", generator=g)
+        work = torch.empty(b.cfd_filter_workspace(H.N, n_s, n_b, n_p, ph, px), dtype=torch.uint8, device="cuda")
+        mu = torch.empty(n_s, 2 * n_p, dtype=torch.float64, device="cuda")
+        blk = b.block_of(X)
+
+        def once():
+            b._check(b.lib().cfd_filter(H.ref(), BOUNDS[0], BOUNDS[1], -0.3, 0.3, n_p, blk, n_b, b._ptr(work),
+                                        work.numel(), b._ptr(mu), b._stream()))
+        ts = []
+        for r in range(max(a.warmup, 1) + max(a.steps, 1)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            once()
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= max(a.warmup, 1):
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        t_step = statistics.median(ts) / (n_p * (n_s // n_b))
+        sb = model.step_bytes(H.N, H.nnz, n_b, ph)
+        row = {"lattice": "x".join(map(str, lat)), "N": H.N, "nnz": H.nnz, "filter": ph, "block": px, "n_s": n_s,
+               "n_b": n_b, "n_p": n_p, "ms_per_step": round(1e3 * t_step, 4), "gbs": round(sb / t_step / 1e9, 1),
+               "frac_hbm": round(sb / t_step / 1e9 / hbm, 4),
+               "gflops_paper": round(model.step_flops(H.N, H.nnz, n_b) / t_step / 1e9, 1),
+               "gflops_pipe": round(model.step_fma_flops(H.N, H.nnz, n_b, packed=True)
+                                    / t_step / 1e9, 1)}
+        if ph == "c128":
+            row["frac_fp64_peak"] = round(row["gflops_pipe"] / FP64_PEAK_GFLOPS, 4)
+        rows.append(row)
+        del X, work, H
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "fused filter SpMMV GB/s and Gflop/s per configuration", "unit": "GB/s",
+                      "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "data": "synthetic",
+                      "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src, "fp64_peak_gflops": round(FP64_PEAK_GFLOPS, 1),
+                      "traffic_model": "nnz (s + 4) + 5 N n_b s bytes per step",
+                      "flops_paper": "(8 nnz + 42 N) n_b per step", "results": rows}))
+
+
+def run_tte(a):
+    """Time to eigenpairs (residual <= 1e-10, cfd_solve from a device-resident
+    random start block, after the untimed matrix build, Lanczos bounds and KPM
+    window) for the fp64 policy and the mixed policy (complex64 filter, fp64
+    SVQB, Rayleigh-Ritz and residuals, then fp64 filter sweeps) on one
+    workload, with the per-eigenvalue difference between the two."""
+    import torch
+    from paper_1803_02156_gb300 import binding as b
+    torch.cuda.set_device(0)
+    w = workloads.ALL[a.tte_workload] if a.tte_workload else WORKLOAD
+    a.n_p, a.n_b = w.n_p, w.n_b
+    p, H, lmin, lmax, lam_l, lam_r = setup_problem(b, w, w.seed, a.storage)
+    res = time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a)
+    print(json.dumps({"metric": "time to eigenpairs, fp64 vs mixed", "unit": "s", "n_gpus": 1, "data": "synthetic",
+                      "higher_is_better": False,
+                      "config": {"workload": w.name, "lattice": list(w.lattice), "N": H.N, "n_s": w.n_s,
+                                 "n_t": w.n_t, "n_p": w.n_p, "n_b": w.n_b, "window": [lam_l, lam_r],
+                                 "bounds": [lmin, lmax]},
+                      "time_to_eigenpairs": res}))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -619,6 +706,10 @@ def main():
         run_fusion(a)
     elif a.mode == "host":
         run_host(a)
+    elif a.mode == "sweep":
+        run_sweep(a)
+    elif a.mode == "tte":
+        run_tte(a)
     else:
         run_gpu(a)
 

@@ -14,6 +14,10 @@ namespace cg = cooperative_groups;
 
 __device__ __forceinline__ size_t round_up_dev(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
 // ------------------------------------------------------ step kernel --
 
 namespace {
@@ -511,9 +515,6 @@ k_cheb_step(const StepArgs<T> A) {
 
 // ------------------------------------------------- TMA-staged general step --
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
@@ -564,11 +565,12 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
 // barrier expects 16 bytes more than are copied, so no wait can succeed, and
 // waits give up after 2^24 cycles.
 // KMAX > 0: every gather of a row's first KMAX slots in flight at once
-// (packed values; registers capped so that two CTAs fit on an SM).  CH > 0:
+// (packed values; registers capped so that two CTAs fit on an SM, three for
+// KMAX <= 8).  CH > 0:
 // the matrix's chunk height, fixed at compile time (packed values; the
 // host launches it only for C == CH and 32-bit gather offsets).
 template <typename T, int NB, int VPT, bool MOM, bool PACK, int KMAX = 0, int CH = 0>
-__global__ void __launch_bounds__(STEP_WARPS * 32, KMAX > 0 ? 2 : 0)
+__global__ void __launch_bounds__(STEP_WARPS * 32, KMAX > 8 ? 2 : (KMAX > 0 ? 3 : 0))
 k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
     using C = cplx_t<T>;
     using V = typename std::conditional<PACK, T, C>::type;
@@ -639,7 +641,7 @@ k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
                 if (r >= n_rows) continue;
                 const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
                 process_row<T, NB, VPT, STEP_GENERAL, MOM, PACK, true, KMAX, CH>(A, i, col_s(b) + rr, val_s(b) + rr,
-                                                                                 log2C, nre, len, j0, cf, uu, wu);
+                                                                             log2C, nre, len, j0, cf, uu, wu);
             }
         }
         // one barrier per chunk: buffer b is refilled only after every thread
@@ -705,7 +707,7 @@ cfd_status launch_one(const StepArgs<T> &A, int grid_cap, cudaStream_t stream) {
         if (!A.status) return fail(CFD_ERR_INTERNAL, "staged step without a status word");
         slots_cap = A.H.slots_bound << A.H.log2C;
         if (slots_cap <= 0) return fail(CFD_ERR_ARG, "matrix has no slot bound; cannot stage");
-        smem = 2 * round_up((size_t)slots_cap * 4, 16) + 2 * (size_t)slots_cap * sizeof(V);
+        smem = 2 * round_up((size_t)slots_cap * 4, 16) + round_up(2 * (size_t)slots_cap * sizeof(V), 16);
         if (smem > 200 * 1024) return fail(CFD_ERR_ARG, "chunk too large to stage (%zu bytes)", smem);
     }
     auto kern = k_cheb_step<T, NB, VPT, KIND, MOM, PACK>;
@@ -725,22 +727,19 @@ cfd_status launch_one(const StepArgs<T> &A, int grid_cap, cudaStream_t stream) {
             skern = fixed ? k_cheb_step_staged<T, NB, VPT, MOM, PACK, STEP_GATHER_ALL, 32>
                           : k_cheb_step_staged<T, NB, VPT, MOM, PACK, STEP_GATHER_ALL>;
         else if (kmax == 8)
-            skern = k_cheb_step_staged<T, NB, VPT, MOM, PACK, 8>;
+            skern = fixed ? k_cheb_step_staged<T, NB, VPT, MOM, PACK, 8, 32> : k_cheb_step_staged<T, NB, VPT, MOM, PACK, 8>;
         else if (fixed)
             skern = k_cheb_step_staged<T, NB, VPT, MOM, PACK, 0, 32>;
     }
     // occupancy cache per device and kernel variant: 0 plain; staged generic
-    // 1 (groups of four), 2 (8 at once), 3 (16 at once); staged fixed 4, 5 (16 at once)
-    static int occ[64][6] = {{0}};
-    static size_t occ_smem[64][6] = {{0}};
+    // 1 (groups of four), 2 (8 at once), 3 (16 at once); staged fixed 4, 5, 6
+    static int occ[64][7] = {{0}};
+    static size_t occ_smem[64][7] = {{0}};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
     int which = 0;
-    if (staged) {
-        if (fixed && kmax != 8) which = kmax == STEP_GATHER_ALL ? 5 : 4;
-        else which = kmax == STEP_GATHER_ALL ? 3 : (kmax == 8 ? 2 : 1);
-    }
+    if (staged) which = (kmax == STEP_GATHER_ALL ? 3 : (kmax == 8 ? 2 : 1)) + (fixed ? 3 : 0);
     if (occ[dev][which] == 0 || (staged && occ_smem[dev][which] != smem)) {
         int o = 0;
         if (staged) {
