@@ -30,6 +30,10 @@ WORKLOAD = workloads.MEDIUM
 BOUNDS = (-8.6, 8.6)          # contains the Gershgorin interval [-8.5, 8.5] of the gamma = 1 lattice
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# general step on this workload at n_b = 32, from one ncu capture of each
+# kernel as it stands: (filter precision, n_b, value storage) -> bytes.
+PROFILED_TRAFFIC = {("c128", 32, "packed"): 1.516e9, ("c64", 32, "packed"): 0.682e9}
 
 
 def measured_hbm_gbs():
@@ -286,14 +290,16 @@ def run_gpu(a):
         fma = model.step_fma_flops(N, nnz, n_b, packed=(a.storage == "packed"))
         achieved = fma / t_launch / 1e9
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GFLOPS, 1),
-                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                "traffic": PROFILED_TRAFFIC.get((prec, n_b, a.storage)),
                 "peak_source": "nominal FP64 FMA rate (152 SMs x 2/clk x 2.07 GHz)",
                 "kernel": "k_cheb_step_staged<double,%d,%d,moments,%s>" % (n_b, 2 if n_b >= 16 else 1, a.storage),
                 "avg_launch_ms": round(1e3 * t_launch, 4), "hbm_gbs": round(gbs_launch, 1),
                 "hbm_frac": round(gbs_launch / hbm, 4)}
     else:
         roof = {"bound": "hbm", "achieved": round(gbs_launch, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(gbs_launch / hbm, 4), "traffic": None, "peak_source": hbm_src,
+                "frac": round(gbs_launch / hbm, 4), "traffic": PROFILED_TRAFFIC.get((prec, n_b, a.storage)),
+                "peak_source": hbm_src,
                 "kernel": "k_cheb_step_staged<float,%d,2,moments,%s%s>" % (
                     n_b, a.storage, ",chunk height 32" if a.storage == "packed" else ""),
                 "avg_launch_ms": round(1e3 * t_launch, 4)}

@@ -24,16 +24,16 @@ cfd_status fail(cfd_status st, const char *fmt, ...) {
 void clear_error() { g_last_error[0] = 0; }
 
 int sm_count() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64] = {};   // per device, 0 until first asked
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (cached[dev] == 0) {
-        int n = 0;
+    int n = cached[dev].load();
+    if (n == 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
             n = 1;
-        cached[dev] = n;
+        cached[dev].store(n);
     }
-    return cached[dev];
+    return n;
 }
 
 cfd_status check_matrix(const cfd_matrix *H) {

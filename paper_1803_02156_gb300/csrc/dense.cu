@@ -9,6 +9,7 @@
 // and X M equals Xr Mr with the real representation Mr of M
 // (Mr_2a,2b = Mr_2a+1,2b+1 = Re M_ab, Mr_2a,2b+1 = Im M_ab, Mr_2a+1,2b = -Im M_ab).
 #include <algorithm>
+#include <atomic>
 #include <cooperative_groups.h>
 
 #include "dense.cuh"
@@ -297,12 +298,13 @@ cfd_status project_inplace(double2 *X, int64_t ldx, int64_t n_rows, int n_in, co
     CFD_LAUNCH_CHECK();
     int kin = 2 * n_in, nout = 2 * n_out;
     size_t smem = ((size_t)PJ_ROWS * (kin + 4) + (size_t)PJ_KS * (PJ_NT + 4)) * sizeof(double);
-    static int configured[64] = {0};
+    // the limit is always the same 227 KB, so concurrent first calls may both set it
+    static std::atomic<int> configured[64] = {};
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !configured[dev]) {
+    CFD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !configured[dev].load()) {
         CFD_CUDA(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        configured[dev] = 1;
+        if (dev >= 0 && dev < 64) configured[dev].store(1);
     }
     if (smem > 227 * 1024) return fail(CFD_ERR_ARG, "block too wide for in-place projection (n=%d)", n_in);
     unsigned grid = (unsigned)((n_rows + PJ_ROWS - 1) / PJ_ROWS);

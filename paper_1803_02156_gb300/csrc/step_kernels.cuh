@@ -3,7 +3,9 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cooperative_groups.h>
+#include <mutex>
 #include <type_traits>
 
 #include "filter.cuh"
@@ -731,32 +733,48 @@ cfd_status launch_one(const StepArgs<T> &A, int grid_cap, cudaStream_t stream) {
         else if (fixed)
             skern = k_cheb_step_staged<T, NB, VPT, MOM, PACK, 0, 32>;
     }
-    // occupancy cache per device and kernel variant: 0 plain; staged generic
-    // 1 (groups of four), 2 (8 at once), 3 (16 at once); staged fixed 4, 5, 6
-    static int occ[64][7] = {{0}};
-    static size_t occ_smem[64][7] = {{0}};
+    // Occupancy per device and kernel variant (0 plain; staged generic 1
+    // (groups of four), 2 (8 at once), 3 (16 at once); staged fixed 4, 5, 6),
+    // and the shared-memory limit set on the kernel, which only ever grows so
+    // that a concurrent launch with a larger chunk never finds it lowered.
+    // One mutex per instantiation guards the cache and the attribute.
+    struct Cache {
+        std::mutex mu;
+        int occ[64][7];
+        size_t occ_smem[64][7];
+        size_t attr_smem[64][7];
+    };
+    static Cache cache{};
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) dev = 0;
+    CFD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CFD_ERR_ARG, "device ordinal %d out of range", dev);
     int which = 0;
     if (staged) which = (kmax == STEP_GATHER_ALL ? 3 : (kmax == 8 ? 2 : 1)) + (fixed ? 3 : 0);
-    if (occ[dev][which] == 0 || (staged && occ_smem[dev][which] != smem)) {
-        int o = 0;
-        if (staged) {
+    int resident = 0;
+    {
+        std::lock_guard<std::mutex> lock(cache.mu);
+        if (staged && smem > cache.attr_smem[dev][which]) {
             CFD_CUDA(cudaFuncSetAttribute(skern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, skern, STEP_WARPS * 32, smem));
-            occ_smem[dev][which] = smem;
-        } else {
-            CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, STEP_WARPS * 32, 0));
+            cache.attr_smem[dev][which] = smem;
         }
-        occ[dev][which] = std::max(1, std::min(o, STEP_MAX_CTAS_PER_SM));
+        if (cache.occ[dev][which] == 0 || (staged && cache.occ_smem[dev][which] != smem)) {
+            int o = 0;
+            if (staged) {
+                CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, skern, STEP_WARPS * 32, smem));
+                cache.occ_smem[dev][which] = smem;
+            } else {
+                CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, STEP_WARPS * 32, 0));
+            }
+            cache.occ[dev][which] = std::max(1, std::min(o, STEP_MAX_CTAS_PER_SM));
+        }
+        resident = cache.occ[dev][which];
     }
     constexpr int RPW = 32 / (NB / VPT);
     const int64_t C = 1LL << A.H.log2C;
     const int64_t passes = (C + STEP_WARPS * RPW - 1) / (STEP_WARPS * RPW);
     const int64_t n_chunks = (A.H.n_rows + C - 1) / C;
     int64_t need = staged ? n_chunks : n_chunks * passes;     // work items
-    int64_t grid = std::min<int64_t>((int64_t)occ[dev][which] * sm_count(), need);
+    int64_t grid = std::min<int64_t>((int64_t)resident * sm_count(), need);
     if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
     grid = std::max<int64_t>(grid, 1);
     if (staged) {
@@ -810,20 +828,20 @@ template <typename T, int NB, int VPT, bool PACK>
 cfd_status launch_persistent_nbp(const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> *xb, int64_t ldx,
                                  int n_p, int grid_cap, cudaStream_t stream) {
     auto kern = k_cheb_persistent<T, NB, VPT, PACK>;
-    static int occ[64] = {0};
+    static std::atomic<int> occ[64] = {};      // resident CTAs per SM, per device (0: not yet known)
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) dev = 0;
-    if (occ[dev] == 0) {
+    CFD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CFD_ERR_ARG, "device ordinal %d out of range", dev);
+    if (occ[dev].load() == 0) {
         int o = 0;
         CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, STEP_WARPS * 32, 0));
-        occ[dev] = std::max(1, std::min(o, STEP_MAX_CTAS_PER_SM));
+        occ[dev].store(std::max(1, std::min(o, STEP_MAX_CTAS_PER_SM)));
     }
     constexpr int RPW = 32 / (NB / VPT);
     const int64_t C = 1LL << A.H.log2C;
     const int64_t passes = (C + STEP_WARPS * RPW - 1) / (STEP_WARPS * RPW);
     int64_t need = (A.H.n_rows + C - 1) / C * passes;       // work items (chunk passes)
-    int64_t grid = std::min<int64_t>((int64_t)occ[dev] * sm_count(), need);
+    int64_t grid = std::min<int64_t>((int64_t)occ[dev].load() * sm_count(), need);
     if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
     grid = std::max<int64_t>(grid, 1);
     StepArgs<T> a = A;
