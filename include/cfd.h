@@ -219,6 +219,10 @@ typedef struct cfd_block {
  * blocks of n_b vectors with degree n_p, matrix precision prec_H and block
  * precision prec_X.  Flag bits above the low byte (CFD_PACK_RI) are ignored
  * by this and the other workspace queries.  Returns 0 for invalid sizes.
+ * Besides the two N x n_b recurrence blocks it holds the matrix values
+ * prepared once per call as 2 alpha (H - beta) for the general steps, sized
+ * for 13 stored entries per row (the matrices cfd_build_matrix and
+ * cfd_build_batch make); a matrix with more is rejected with CFD_ERR_ARG.
  */
 size_t cfd_filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X);
 
@@ -417,7 +421,7 @@ cfd_status cfd_workspace_status(const void *work, cudaStream_t stream);
  * The scratch is a 64 MiB array inside the library, one copy on every device
  * that loads it, kept until the process exits.  Problems whose
  * cfd_filter_workspace(...) exceeds CFD_NOALLOC_SCRATCH_BYTES are rejected
- * with CFD_ERR_ARG (roughly N * n_b <= 1.9e6 for complex double blocks).
+ * with CFD_ERR_ARG (for complex double roughly N (32 n_b + 208) bytes <= 64 MiB, e.g. N <= 54000 at n_b = 32).
  * Nothing is allocated: no cudaMalloc/cudaFree and no allocating library call.
  *
  * The first call on a device looks up the scratch array's device address

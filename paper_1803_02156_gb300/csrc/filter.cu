@@ -59,6 +59,73 @@ cfd_status launch_filter_coeffs(double alpha, double beta, double lam_l, double 
     return CFD_OK;
 }
 
+// One thread per row position r of the padded SELL layout (chunk r >> log2C,
+// row r & (C - 1) within it): its slots k < the chunk's length sit at
+// chunk_ptr + k C + row.  The canonical row index i (through perm) tells the
+// diagonal slot, the one whose column is i; rows past the end have none.
+// Computed in fp64 and rounded once to the storage precision.
+template <typename T, bool PACK>
+__global__ void k_prepare_values(SellView<T> H, int64_t n_pos, double alpha, double beta, const int32_t *chunk_rid,
+                                 const double *rcoef, int64_t rcoef_ld, void *out) {
+    using C = cplx_t<T>;
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_pos) return;
+    const int64_t ch = r >> H.log2C;
+    const int64_t base = H.chunk_ptr[ch] + (r & ((1 << H.log2C) - 1));
+    const int cl = H.chunk_len[ch];
+    const int len = PACK ? (cl & 0xffff) + (cl >> 16) : cl;
+    const int64_t i = r < H.n_rows ? (H.perm ? (int64_t)H.perm[r] : r) : -2;   // -2 never matches a column
+    if (chunk_rid) {
+        const double *rc = rcoef + (int64_t)chunk_rid[ch] * rcoef_ld;
+        alpha = rc[0];
+        beta = rc[1];
+    }
+    const double a2 = 2.0 * alpha;
+    for (int k = 0; k < len; ++k) {
+        const int64_t s = base + ((int64_t)k << H.log2C);
+        const bool diag = H.col[s] == i;
+        if constexpr (PACK) {
+            const double h = (double)H.pval[s];
+            static_cast<T *>(out)[s] = (T)(diag ? a2 * (h - beta) : a2 * h);
+        } else {
+            const C h = H.val[s];
+            C v;
+            v.x = (T)(diag ? a2 * ((double)h.x - beta) : a2 * (double)h.x);
+            v.y = (T)(a2 * (double)h.y);
+            static_cast<C *>(out)[s] = v;
+        }
+    }
+}
+
+template <typename T>
+static cfd_status prepare_values_t(const cfd_matrix *H, double alpha, double beta, const int32_t *chunk_rid,
+                                   const double *rcoef, int64_t rcoef_ld, void *out, size_t out_bytes,
+                                   cudaStream_t stream) {
+    const SellView<T> v = sell_view<T>(H);
+    const size_t bytes = (size_t)H->n_slots * (v.packed ? sizeof(T) : sizeof(cplx_t<T>));
+    if (bytes > out_bytes)
+        return fail(CFD_ERR_ARG, "matrix stores %lld slots, more than the filter workspace prepares (%d per row)",
+                    (long long)H->n_slots, kMaxRowSlots);
+    const int64_t n_pos = H->n_chunks << v.log2C;
+    if (n_pos == 0) return CFD_OK;
+    const unsigned grid = (unsigned)((n_pos + 255) / 256);
+    if (v.packed)
+        k_prepare_values<T, true><<<grid, 256, 0, stream>>>(v, n_pos, alpha, beta, chunk_rid, rcoef, rcoef_ld, out);
+    else
+        k_prepare_values<T, false><<<grid, 256, 0, stream>>>(v, n_pos, alpha, beta, chunk_rid, rcoef, rcoef_ld, out);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    return CFD_OK;
+}
+
+cfd_status launch_prepare_values(const cfd_matrix *H, double alpha, double beta, const int32_t *chunk_rid,
+                                 const double *rcoef, int64_t rcoef_ld, void *out, size_t out_bytes,
+                                 cudaStream_t stream) {
+    if (H->prec == CFD_C128)
+        return prepare_values_t<double>(H, alpha, beta, chunk_rid, rcoef, rcoef_ld, out, out_bytes, stream);
+    return prepare_values_t<float>(H, alpha, beta, chunk_rid, rcoef, rcoef_ld, out, out_bytes, stream);
+}
+
 // ------------------------------------------------------ step dispatch --
 
 // The step kernels are compiled in four translation units (fp64/fp32 x
@@ -169,6 +236,12 @@ int default_vpt(int prec, int n_b) {
     return n_b >= 16 ? 2 : 1;
 }
 
+// Bytes of prepared values for a matrix of N rows: kMaxRowSlots complex
+// values per row, rows padded to whole chunks of the largest height (128).
+static size_t prep_bytes(int64_t N, int prec_H) {
+    return (size_t)kMaxRowSlots * (size_t)(N + 127) * (prec_H == CFD_C128 ? 16 : 8);
+}
+
 size_t filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X) {
     (void)n_s;
     size_t sH = prec_H == CFD_C128 ? 16 : 8;
@@ -177,6 +250,7 @@ size_t filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int pr
     c.take<char>((size_t)N * n_b * sH);                      // V_a
     c.take<char>((size_t)N * n_b * sH);                      // V_b
     if (prec_H != prec_X) c.take<char>((size_t)N * n_b * 8); // narrowed X block
+    c.take<char>(prep_bytes(N, prec_H));                      // prepared matrix values
     c.take<double>((size_t)n_p + 1);                          // weights
     c.take<double>((size_t)n_p * n_b * 2);                    // raw dots
     c.take<double>((size_t)STEP_MAX_GRID * 2 * n_b);       // CTA partials
@@ -214,6 +288,12 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
     A.gather = P.gather;
     A.fixed_chunk = P.fixed_chunk;
     A.status = ws.status;
+    if (P.staged && !P.persistent) {
+        // the staged general steps read 2 alpha (H - beta), prepared once per call
+        CFD_TRY(launch_prepare_values(H, P.alpha, P.beta, P.chunk_rid, P.rcoef, P.rcoef_ld, ws.prep, ws.prep_bytes,
+                                      stream));
+        A.prep_val = ws.prep;
+    }
     C *va = static_cast<C *>(ws.va), *vb = static_cast<C *>(ws.vb);
     const int n_blocks = X.n_cols / n_b;
     const size_t sX = X.prec == CFD_C128 ? 16 : 8;
@@ -283,6 +363,8 @@ static FilterScratch carve_filter(const cfd_matrix *H, const cfd_block &X, int n
     ws.va = c.take<char>((size_t)H->n_rows * n_b * sH);
     ws.vb = c.take<char>((size_t)H->n_rows * n_b * sH);
     ws.xn = (H->prec != X.prec) ? c.take<char>((size_t)H->n_rows * n_b * 8) : nullptr;
+    ws.prep_bytes = prep_bytes(H->n_rows, H->prec);
+    ws.prep = c.take<char>(ws.prep_bytes);
     ws.gc = c.take<double>((size_t)n_p + 1);
     ws.raw = c.take<double>((size_t)n_p * n_b * 2);
     ws.partial = c.take<double>((size_t)STEP_MAX_GRID * 2 * n_b);
@@ -347,6 +429,9 @@ cfd_status kpm_impl(const cfd_matrix *H, double lmin, double lmax, int n_p, cons
     const int vpt = default_vpt(H->prec, n_b);
     const size_t s = H->prec == CFD_C128 ? 16 : 8;
     CFD_TRY(launch_filter_coeffs(alpha, beta, lmin, lmax, n_p, ws.gc, stream));   // weights unused
+    const bool staged = default_staged(H->prec);
+    if (staged)
+        CFD_TRY(launch_prepare_values(H, alpha, beta, nullptr, nullptr, 0, ws.prep, ws.prep_bytes, stream));
     for (int b = 0; b < R.n_cols / n_b; ++b) {
         const void *rb = static_cast<const char *>(R.ptr) + (size_t)b * n_b * s;
         double *mu = moments + (int64_t)b * n_b * 2 * n_p;
@@ -354,8 +439,9 @@ cfd_status kpm_impl(const cfd_matrix *H, double lmin, double lmax, int n_p, cons
             StepArgs<double> A;
             A.H = sell_view<double>(H);
             A.gc = ws.gc; A.partial = ws.partial; A.ticket = ws.ticket; A.status = ws.status; A.beta = beta;
-            A.staged = default_staged(H->prec);
+            A.staged = staged;
             A.gather = default_gather(H->prec);
+            A.prep_val = staged ? ws.prep : nullptr;
             double2 *va = static_cast<double2 *>(ws.va), *vb = static_cast<double2 *>(ws.vb);
             A.vin = static_cast<const double2 *>(rb); A.ldin = R.ld; A.w = va; A.ldw = n_b; A.x = nullptr;
             A.a = alpha; A.p = 1; A.dots = ws.raw;
@@ -372,8 +458,9 @@ cfd_status kpm_impl(const cfd_matrix *H, double lmin, double lmax, int n_p, cons
             StepArgs<float> A;
             A.H = sell_view<float>(H);
             A.gc = ws.gc; A.partial = ws.partial; A.ticket = ws.ticket; A.status = ws.status; A.beta = beta;
-            A.staged = default_staged(H->prec);
+            A.staged = staged;
             A.gather = default_gather(H->prec);
+            A.prep_val = staged ? ws.prep : nullptr;
             float2 *va = static_cast<float2 *>(ws.va), *vb = static_cast<float2 *>(ws.vb);
             A.vin = static_cast<const float2 *>(rb); A.ldin = R.ld; A.w = va; A.ldw = n_b; A.x = nullptr;
             A.a = alpha; A.p = 1; A.dots = ws.raw;

@@ -50,6 +50,11 @@ struct StepArgs {
     // gathers in flight per row in staged general steps of packed matrices:
     // STEP_GATHER_ALL (all of the first 16 slots at once) or groups of four
     int gather = 0;
+    // staged general steps: the matrix values prepared as 2 alpha (H - beta)
+    // (launch_prepare_values; same SELL layout and storage as H's values);
+    // required by the staged kernel, which then starts each row sum at
+    // -V_prev and needs no shift, scale or subtraction
+    const void *prep_val = nullptr;
     // staged packed steps of C = 32 matrices: the kernel compiled for that
     // chunk height (>= 0) or the generic one (< 0); results are the same
     int fixed_chunk = 0;
@@ -82,9 +87,15 @@ struct FilterPlan {
     int64_t rcoef_ld = 0;
 };
 
+// Stored entries per row of the matrices this library builds (Topi: the
+// on-site term and two per neighbour): bounds the prepared-values buffer.
+constexpr int kMaxRowSlots = 13;
+
 struct FilterScratch {
     int *status;            // device status word (first bytes of the workspace)
     void *va, *vb, *xn;
+    void *prep;             // prepared matrix values (2 alpha (H - beta)), prep_bytes long
+    size_t prep_bytes;
     double *gc, *raw, *partial;
     unsigned *ticket;
     int grid_cap;
@@ -99,6 +110,13 @@ size_t filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int pr
 cfd_status validate_block(const cfd_block &X, int64_t n_rows);
 cfd_status launch_filter_coeffs(double alpha, double beta, double lam_l, double lam_r, int n_p,
                                 double *gc, cudaStream_t stream);
+// Values of 2 alpha (H - beta) in H's SELL layout and storage into out
+// (capacity out_bytes): every stored value times 2 alpha, beta subtracted
+// first on the diagonal; in a batch (chunk_rid set) each chunk takes its
+// realisation's alpha and beta from rcoef (row stride rcoef_ld).
+cfd_status launch_prepare_values(const cfd_matrix *H, double alpha, double beta, const int32_t *chunk_rid,
+                                 const double *rcoef, int64_t rcoef_ld, void *out, size_t out_bytes,
+                                 cudaStream_t stream);
 cfd_status launch_moments(const double *raw, int n_p, int nb, double *mu, int64_t ld_mu,
                           cudaStream_t stream);
 cfd_status launch_narrow(const double2 *src, int64_t lds, float2 *dst, int64_t ldd, int64_t n_rows,

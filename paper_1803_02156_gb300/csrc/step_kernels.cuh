@@ -328,15 +328,22 @@ struct StepCoef {
 // KMAX > 0 (packed values): the first KMAX slots' gathers all in flight at
 // once (packed_all); 0: groups of four.  CH > 0 (staged packed rows): chunk
 // height fixed at compile time, 32-bit gather offsets (packed_row_fixed).
-template <typename T, int NB, int VPT, int KIND, bool MOM, bool PACK, bool SMEM, int KMAX = 0, int CH = 0>
+// PREP (general steps): the row's values are those of 2 alpha (H - beta)
+// (launch_prepare_values), so the row sum started at -V_prev is the new
+// vector itself: W = 2 alpha (H - beta) V_cur - V_prev costs the sum alone,
+// and V_cur's own row is read only for the moments.
+template <typename T, int NB, int VPT, int KIND, bool MOM, bool PACK, bool SMEM, int KMAX = 0, int CH = 0,
+          bool PREP = false>
 __device__ __forceinline__ void process_row(const StepArgs<T> &A, int64_t i, const int32_t *colp, const void *valp,
                                             int log2C, int nre, int len, int j0, const StepCoef<T, KIND> &cf,
                                             MomentAcc<T> (&uu)[VPT], MomentAcc<T> (&wu)[VPT]) {
     using C = cplx_t<T>;
     constexpr int UNR = 4;
+    static_assert(!PREP || KIND == STEP_GENERAL, "prepared values only in general steps");
     // operands of the epilogue do not depend on the gathers: issue their
     // (streaming) loads first so their latency overlaps the SpMMV
-    const Pack<C, VPT> u = ld_nc<C, VPT>(A.vin + i * A.ldin + j0);
+    Pack<C, VPT> u;
+    if (!PREP || MOM) u = ld_nc<C, VPT>(A.vin + i * A.ldin + j0);
     // A.x == nullptr: moments only (Algorithm 1 without line 12), X untouched;
     // step 2 then needs the start block's row i, which is V_prev's role here
     Pack<C, VPT> wo, xo;
@@ -346,7 +353,7 @@ __device__ __forceinline__ void process_row(const StepArgs<T> &A, int64_t i, con
 
     C acc[VPT];
 #pragma unroll
-    for (int q = 0; q < VPT; ++q) acc[q] = cmake<T>(0, 0);
+    for (int q = 0; q < VPT; ++q) acc[q] = PREP ? cmake<T>(-wo.v[q].x, -wo.v[q].y) : cmake<T>(0, 0);
     if constexpr (PACK && CH > 0) {
         const uint32_t ld16 = (uint32_t)((A.ldin * (int64_t)sizeof(C)) >> 4);
         packed_row_fixed<T, VPT, UNR, KMAX, CH>(reinterpret_cast<const char *>(A.vin + j0), ld16, colp,
@@ -387,8 +394,12 @@ __device__ __forceinline__ void process_row(const StepArgs<T> &A, int64_t i, con
         Pack<C, VPT> xn;
 #pragma unroll
         for (int q = 0; q < VPT; ++q) {
-            wn.v[q].x = fma(a, fma(-beta, u.v[q].x, acc[q].x), -wo.v[q].x);
-            wn.v[q].y = fma(a, fma(-beta, u.v[q].y, acc[q].y), -wo.v[q].y);
+            if (PREP) {
+                wn.v[q] = acc[q];
+            } else {
+                wn.v[q].x = fma(a, fma(-beta, u.v[q].x, acc[q].x), -wo.v[q].x);
+                wn.v[q].y = fma(a, fma(-beta, u.v[q].y, acc[q].y), -wo.v[q].y);
+            }
             xn.v[q].x = fma(g0, wn.v[q].x, xo.v[q].x);
             xn.v[q].y = fma(g0, wn.v[q].y, xo.v[q].y);
         }
@@ -559,7 +570,9 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
 // whole chunks grid-stride; one thread copies the next chunk's column indices
 // and values with two TMA bulk copies into the other half of a double buffer
 // while the CTA computes the current chunk from shared memory, so a row's
-// critical path holds only its V_cur gathers.  Slot counts of a chunk are
+// critical path holds only its V_cur gathers.  The values are those of
+// 2 alpha (H - beta) (A.prep_val), so each row sum starts at -V_prev and is
+// the new vector when it ends.  Slot counts of a chunk are
 // multiples of C >= 4, so every copy is 16-byte aligned and sized.  A wait
 // that expires (after ~2^32 cycles, about two seconds) records
 // CFD_ERR_TIMEOUT in *A.status and the CTA returns after draining its own
@@ -595,7 +608,8 @@ k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
     const int chunk_h = CH > 0 ? CH : 1 << log2C;
     const int64_t n_rows = A.H.n_rows;
     const int64_t n_chunks = (n_rows + chunk_h - 1) >> log2C;
-    const V *gval = PACK ? reinterpret_cast<const V *>(A.H.pval) : reinterpret_cast<const V *>(A.H.val);
+    // the values of 2 alpha (H - beta), prepared once per filter call
+    const V *gval = reinterpret_cast<const V *>(A.prep_val);
     const uint32_t tx_extra = A.staged == 2 ? 16u : 0u;
     const long long limit = A.staged == 2 ? (1LL << 24) : (1LL << 32);
     StepCoef<T, STEP_GENERAL> cf;
@@ -642,8 +656,8 @@ k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
                 const int64_t r = (c << log2C) + rr;
                 if (r >= n_rows) continue;
                 const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
-                process_row<T, NB, VPT, STEP_GENERAL, MOM, PACK, true, KMAX, CH>(A, i, col_s(b) + rr, val_s(b) + rr,
-                                                                             log2C, nre, len, j0, cf, uu, wu);
+                process_row<T, NB, VPT, STEP_GENERAL, MOM, PACK, true, KMAX, CH, true>(
+                A, i, col_s(b) + rr, val_s(b) + rr, log2C, nre, len, j0, cf, uu, wu);
             }
         }
         // one barrier per chunk: buffer b is refilled only after every thread
@@ -707,6 +721,7 @@ cfd_status launch_one(const StepArgs<T> &A, int grid_cap, cudaStream_t stream) {
     size_t smem = 0;
     if (staged) {
         if (!A.status) return fail(CFD_ERR_INTERNAL, "staged step without a status word");
+        if (!A.prep_val) return fail(CFD_ERR_INTERNAL, "staged step without prepared matrix values");
         slots_cap = A.H.slots_bound << A.H.log2C;
         if (slots_cap <= 0) return fail(CFD_ERR_ARG, "matrix has no slot bound; cannot stage");
         smem = 2 * round_up((size_t)slots_cap * 4, 16) + round_up(2 * (size_t)slots_cap * sizeof(V), 16);

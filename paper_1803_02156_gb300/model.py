@@ -48,11 +48,15 @@ def step_flops(N, nnz, n_b):
     return (8 * nnz + 42 * N) * n_b
 
 
-def step_fma_flops(N, nnz, n_b, packed=False):
-    """Flops the multiply-add pipe executes for one fused step: (8 nnz + 20 N) n_b
-    with complex matrix values; (4 nnz + 20 N) n_b when every value is stored as
-    one real-or-imaginary scalar (two fused multiply-adds per nonzero)."""
-    return ((4 if packed else 8) * nnz + 20 * N) * n_b
+def step_fma_flops(N, nnz, n_b, packed=False, prepared=False):
+    """Flops the multiply-add pipe must execute for one fused step with
+    moments: (8 nnz + 20 N) n_b with complex matrix values; (4 nnz + 20 N) n_b
+    when every value is stored as one real-or-imaginary scalar (two fused
+    multiply-adds per nonzero).  prepared: the step reads the values of
+    2 alpha (H - beta), prepared once per filter application, and starts each
+    row sum at -V_prev, so the shift, scale and subtraction (8 flops per row
+    and vector) vanish: (4 or 8) nnz n_b + 12 N n_b (X update, two dots)."""
+    return ((4 if packed else 8) * nnz + (12 if prepared else 20) * N) * n_b
 
 
 def intensity(n_b, nnzr=13, prec="c128"):

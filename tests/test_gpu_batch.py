@@ -56,7 +56,10 @@ def _windows(b):
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_batched_filter_equals_looped(b, persistent, prec):
     """Per realisation the batched filter equals cfd_filter on that realisation
-    alone, bit for bit (same kernel arithmetic, same weights)."""
+    alone, bit for bit (same kernel arithmetic, same weights, same prepared
+    matrix values).  The persistent launch runs the unstaged general step, so
+    its reference is the unstaged per-realisation filter (the staged step's
+    prepared values round differently)."""
     import torch
     dt = torch.complex128 if prec == "c128" else torch.complex64
     B = b.cfd_build_batch(_params(b), 32, 1, prec)
@@ -74,7 +77,7 @@ def test_batched_filter_equals_looped(b, persistent, prec):
         N = 4 * nx * ny * nz
         H = b.cfd_build_matrix(b.topi_params(nx, ny, nz, seed=s), 32, 1, prec)
         Y = blocks[r].clone()
-        b.cfd_filter(H, w[r][0], w[r][1], w[r][2], w[r][3], n_p, Y, n_b)
+        b.cfd_filter_ex(H, w[r][0], w[r][1], w[r][2], w[r][3], n_p, Y, n_b, staged=-1 if persistent else 0)
         got = X[B.row_off[r]:B.row_off[r] + N]
         assert torch.equal(got, Y), r
         pad = X[B.row_off[r] + N:B.row_off[r + 1]]
@@ -101,8 +104,9 @@ def test_batched_filter_vs_oracle(b):
 
 @pytest.mark.parametrize("prec,n_b,vpt", [("c128", 32, 1), ("c128", 32, 2), ("c64", 16, 1), ("c64", 64, 2)])
 def test_persistent_and_options_bitwise(b, prec, n_b, vpt):
-    """The single-launch persistent filter and every vectors-per-thread choice
-    give the per-step result bit for bit."""
+    """Every vectors-per-thread choice gives the per-step result bit for bit;
+    the single-launch persistent filter (unstaged general steps) gives the
+    unstaged per-step result bit for bit, and the staged one to rounding."""
     import torch
     dt = torch.complex128 if prec == "c128" else torch.complex64
     L = (10, 9, 6)
@@ -110,10 +114,16 @@ def test_persistent_and_options_bitwise(b, prec, n_b, vpt):
     X0 = torch.from_numpy(inputs.gaussian_block(H.N, 64, seed=3)).to(dt).cuda()
     ref = X0.clone()
     b.cfd_filter(H, -8.6, 8.6, -0.5, 0.5, 80, ref, n_b)
-    for pers in (0, 1):
-        Y = X0.clone()
-        b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 80, Y, n_b, vpt=vpt, persistent=pers, grid_cap=200 if pers else 0)
-        assert torch.equal(Y, ref)
+    ref_unstaged = X0.clone()
+    b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 80, ref_unstaged, n_b, staged=-1)
+    Y = X0.clone()
+    b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 80, Y, n_b, vpt=vpt)
+    assert torch.equal(Y, ref)
+    Y = X0.clone()
+    b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 80, Y, n_b, vpt=vpt, persistent=1, grid_cap=200)
+    assert torch.equal(Y, ref_unstaged)
+    tol = 1e-12 if prec == "c128" else 80 * 13 * 2.0 ** -24
+    assert (torch.linalg.norm(Y - ref) / torch.linalg.norm(ref)).item() < tol
 
 
 def test_graph_capture_replays_filter(b):
@@ -209,9 +219,13 @@ def test_batched_solve_equals_single(b):
 
 @pytest.mark.parametrize("prec,n_b,C", [("c64p", 32, 32), ("c64", 16, 8), ("c128p", 32, 16), ("c128", 64, 32),
                                         ("c64p", 64, 128)])
-def test_staged_kernel_bitwise(b, prec, n_b, C):
-    """Staging the matrix chunks through shared memory changes only where the
-    slot words are read from: the filtered block is the same bit for bit."""
+def test_staged_kernel_matches_unstaged(b, prec, n_b, C):
+    """The staged general step reads matrix values prepared as
+    2 alpha (H - beta) from shared memory and starts each row sum at -V_prev;
+    the unstaged step sums H V_cur, then shifts, scales and subtracts.  Both
+    compute the same recurrence, rounded differently: the filtered blocks
+    agree to rounding (fp64: 1e-12 relative; fp32: the n_p * 13 * 2^-24
+    bound of the complex64 filter)."""
     import torch
     dt = torch.complex128 if prec.startswith("c128") else torch.complex64
     L = (13, 11, 7)
@@ -222,7 +236,8 @@ def test_staged_kernel_bitwise(b, prec, n_b, C):
         Y = X0.clone()
         b.cfd_filter_ex(H, -8.6, 8.6, -0.4, 0.6, 45, Y, n_b, staged=staged)
         outs.append(Y)
-    assert torch.equal(outs[0], outs[1])
+    tol = 1e-12 if dt == torch.complex128 else 45 * 13 * 2.0 ** -24
+    assert (torch.linalg.norm(outs[0] - outs[1]) / torch.linalg.norm(outs[0])).item() < tol
 
 
 def test_staged_timeout_is_reported(b):
