@@ -461,28 +461,78 @@ __device__ __forceinline__ void step_rows(const StepArgs<T> &A, MomentAcc<T> (&u
     }
 }
 
+// Arithmetic of the moment reductions.  fp64 steps add in fp64.  fp32 steps
+// add double-float pairs (hi + lo, Knuth's TwoSum, about 44 significant
+// bits) on the fp32 pipe: GB300 runs fp64 at 1/64 of the fp32 rate, and the
+// fp64 reductions after the rows formed a tail of several microseconds per
+// complex64 step.  A cross-CTA partial is one 8-byte word either way (a
+// double, or the pair as float2); the reduced dot is widened to fp64 once.
+template <typename T> struct MomentRed;
+
+template <> struct MomentRed<double> {
+    using R = double;
+    static __device__ __forceinline__ R from(const MomentAcc<double> &m) { return m.value(); }
+    static __device__ __forceinline__ R zero() { return 0.0; }
+    static __device__ __forceinline__ R add(R a, R b) { return a + b; }
+    static __device__ __forceinline__ R shfl_xor(R a, int off) { return __shfl_xor_sync(0xffffffffu, a, off); }
+    static __device__ __forceinline__ void store(double *p, R a) { *p = a; }
+    static __device__ __forceinline__ R load(const double *p) { return __ldcg(p); }
+    static __device__ __forceinline__ double widen(R a) { return a; }
+};
+
+template <> struct MomentRed<float> {
+    struct R { float hi, lo; };
+    // (hi, lo) with |lo| <= ulp(hi) / 2 from an unnormalised pair
+    static __device__ __forceinline__ R fast_two_sum(float a, float b) {
+        const float h = a + b;
+        return R{h, b - (h - a)};
+    }
+    // Kahan's running sum s with compensation c stands for s - c
+    static __device__ __forceinline__ R from(const MomentAcc<float> &m) { return fast_two_sum(m.s, -m.c); }
+    static __device__ __forceinline__ R zero() { return R{0.f, 0.f}; }
+    static __device__ __forceinline__ R add(R a, R b) {
+        const float s = a.hi + b.hi;                     // TwoSum of the high parts
+        const float bv = s - a.hi;
+        const float e = ((a.hi - (s - bv)) + (b.hi - bv)) + (a.lo + b.lo);
+        return fast_two_sum(s, e);
+    }
+    static __device__ __forceinline__ R shfl_xor(R a, int off) {
+        return R{__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
+    }
+    static __device__ __forceinline__ void store(double *p, R a) {
+        *reinterpret_cast<float2 *>(p) = make_float2(a.hi, a.lo);
+    }
+    static __device__ __forceinline__ R load(const double *p) {
+        const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+        return R{v.x, v.y};
+    }
+    static __device__ __forceinline__ double widen(R a) { return (double)a.hi + (double)a.lo; }
+};
+
 // Deterministic reduction of the threads' moment sums: warps (shuffles), the
 // CTA (shared memory, fixed order), then across CTAs by the last CTA to finish
 // (ticket counter), each in a fixed order.
 template <typename T, int NB, int VPT>
 __device__ __forceinline__ void reduce_moments(const StepArgs<T> &A, MomentAcc<T> (&uu)[VPT],
                                                MomentAcc<T> (&wu)[VPT]) {
+    using Op = MomentRed<T>;
+    using R = typename Op::R;
     constexpr int TPR = NB / VPT;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int sub = lane / TPR;
     const int j0 = (lane % TPR) * VPT;
-    __shared__ double red[STEP_WARPS][NB][2];
+    __shared__ R red[STEP_WARPS][NB][2];
     __shared__ bool last_cta;
-    double s_uu[VPT], s_wu[VPT];
+    R s_uu[VPT], s_wu[VPT];
 #pragma unroll
     for (int q = 0; q < VPT; ++q) {
-        s_uu[q] = uu[q].value();
-        s_wu[q] = wu[q].value();
+        s_uu[q] = Op::from(uu[q]);
+        s_wu[q] = Op::from(wu[q]);
 #pragma unroll
         for (int off = TPR; off < 32; off <<= 1) {
-            s_uu[q] += __shfl_xor_sync(0xffffffffu, s_uu[q], off);
-            s_wu[q] += __shfl_xor_sync(0xffffffffu, s_wu[q], off);
+            s_uu[q] = Op::add(s_uu[q], Op::shfl_xor(s_uu[q], off));
+            s_wu[q] = Op::add(s_wu[q], Op::shfl_xor(s_wu[q], off));
         }
     }
     if (sub == 0) {
@@ -494,10 +544,10 @@ __device__ __forceinline__ void reduce_moments(const StepArgs<T> &A, MomentAcc<T
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 2 * NB; e += blockDim.x) {
-        double s = 0.0;
+        R s = Op::zero();
 #pragma unroll
-        for (int w = 0; w < STEP_WARPS; ++w) s += red[w][e >> 1][e & 1];
-        A.partial[(int64_t)blockIdx.x * 2 * NB + e] = s;
+        for (int w = 0; w < STEP_WARPS; ++w) s = Op::add(s, red[w][e >> 1][e & 1]);
+        Op::store(A.partial + (int64_t)blockIdx.x * 2 * NB + e, s);
     }
     __threadfence();
     __syncthreads();
@@ -506,11 +556,11 @@ __device__ __forceinline__ void reduce_moments(const StepArgs<T> &A, MomentAcc<T
     if (last_cta) {
         __threadfence();
         for (int e = warp; e < 2 * NB; e += STEP_WARPS) {
-            double s = 0.0;
-            for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(A.partial + (int64_t)b * 2 * NB + e);
+            R s = Op::zero();
+            for (int b = lane; b < (int)gridDim.x; b += 32) s = Op::add(s, Op::load(A.partial + (int64_t)b * 2 * NB + e));
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == 0) A.dots[e] = s;
+            for (int off = 16; off > 0; off >>= 1) s = Op::add(s, Op::shfl_xor(s, off));
+            if (lane == 0) A.dots[e] = Op::widen(s);
         }
         if (threadIdx.x == 0) *A.ticket = 0u;
     }
