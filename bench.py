@@ -382,8 +382,18 @@ def time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a):
         out[name] = {"seconds": round(dt, 3), "iters": r.iters, "iters_fp32": r.iters_low, "n_conv": int(r.n_conv),
                      "max_resid": float(rs[conv].max()) if conv.any() else None,
                      "t_filter": round(r.t_filter, 3), "t_orth": round(r.t_orth, 3), "t_rr": round(r.t_rr, 3)}
-    k = min(len(res["fp64"]), len(res["mixed"]))
-    out["max_eval_diff_mixed_vs_fp64"] = float(np.max(np.abs(res["fp64"][:k] - res["mixed"][:k]))) if k else None
+    # each run may converge a pair or two the other has not reached yet (the
+    # levels come in degenerate pairs): match every fp64 eigenvalue with the
+    # nearest mixed one and compare the pairs both runs found
+    a, m = res["fp64"], res["mixed"]
+    if len(a) and len(m):
+        d = np.abs(a[:, None] - m[None, :]).min(axis=1)
+        both = d < 1e-8
+        out["common_pairs"] = int(both.sum())
+        out["max_eval_diff_mixed_vs_fp64"] = float(d[both].max()) if both.any() else None
+    else:
+        out["common_pairs"] = 0
+        out["max_eval_diff_mixed_vs_fp64"] = None
     out["speedup_mixed"] = round(out["fp64"]["seconds"] / out["mixed"]["seconds"], 3)
     out["tol"] = 1e-10
     return out

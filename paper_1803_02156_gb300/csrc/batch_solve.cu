@@ -200,7 +200,7 @@ cfd_status cfd_solve_batched(const cfd_matrix *H, const cfd_matrix *H_low, const
         cudaEventRecord(e[1], stream);
         // SVQB twice (Stathopoulos & Wu), batched over realisations
         for (int pass = 0; pass < 2; ++pass) {
-            CFD_TRY(gram_batched(Xp, n, n, Xp, n, n, d_off, R, S, n, 2 * nn, gw, stream));
+            CFD_TRY(gram_batched(Xp, n, n, Xp, n, n, d_off, R, S, n, 2 * nn, gw, stream, true));
             k_bsvqb_scale<<<dim3((nn + 255) / 256, R), 256, 0, stream>>>(S, n, dsc);
             CFD_COUNT_LAUNCH();
             CFD_LAUNCH_CHECK();
@@ -214,7 +214,7 @@ cfd_status cfd_solve_batched(const cfd_matrix *H, const cfd_matrix *H_low, const
         cudaEventRecord(e[2], stream);
         // Rayleigh-Ritz: Z = H X (block diagonal), G_r = X_r^H Z_r, G_r = Y_r Theta_r Y_r^H
         CFD_TRY(spmmv_block(H, Xp, n, Z, n, n, spart, ticket, nullptr, stream));
-        CFD_TRY(gram_batched(Xp, n, n, Z, n, n, d_off, R, S, n, 2 * nn, gw, stream));
+        CFD_TRY(gram_batched(Xp, n, n, Z, n, n, d_off, R, S, n, 2 * nn, gw, stream, true));
         CFD_TRY(eigh_batched(S, n, 2 * nn, n, R, theta, Q, n, nn, stream));
         CFD_TRY(project_batched(Xp, n, H->n_rows, n, Q, n, nn, d_off, R, pw, stream));
         CFD_TRY(project_batched(Z, n, H->n_rows, n, Q, n, nn, d_off, R, pw, stream));

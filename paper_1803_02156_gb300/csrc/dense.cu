@@ -34,17 +34,29 @@ constexpr int GR_LDS = GR_TILE + 4;  // smem row stride (doubles), conflict-free
 constexpr int GR_THREADS = 256;
 
 // Partial real Gram of a K-range: part[split][m][n] = sum_k A[k][m0 + m] B[k][n0 + n]
-// over rows k of this split.  grid = (tiles_m * tiles_n, splits[, R]).  With
+// over rows k of this split.  grid = (tiles, splits[, R]): all tiles_m x
+// tiles_n output tiles, or with herm (a Hermitian result, ma == nb) only the
+// tiles on and above the diagonal, the fold mirroring the rest.  With
 // row_off (batch), grid.z indexes the realisation whose rows
 // [row_off[z], row_off[z+1]) are split evenly.
 __global__ void __launch_bounds__(GR_THREADS)
 k_gram(const double *__restrict__ A, int64_t lda, int ma, const double *__restrict__ B, int64_t ldb,
-       int nb, int64_t K, int64_t rows_per_split, double *part, const int64_t *row_off) {
+       int nb, int64_t K, int64_t rows_per_split, double *part, const int64_t *row_off, int herm) {
     __shared__ __align__(16) double As[GR_KS][GR_LDS];
     __shared__ __align__(16) double Bs[GR_KS][GR_LDS];
     const int tiles_n = (nb + GR_TILE - 1) / GR_TILE;
-    const int m0 = (blockIdx.x / tiles_n) * GR_TILE;
-    const int n0 = (blockIdx.x % tiles_n) * GR_TILE;
+    int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+    if (herm) {                      // blockIdx.x enumerates the upper tiles row by row
+        int t = blockIdx.x;
+        tm = 0;
+        while (t >= tiles_n - tm) {
+            t -= tiles_n - tm;
+            ++tm;
+        }
+        tn = tm + t;
+    }
+    const int m0 = tm * GR_TILE;
+    const int n0 = tn * GR_TILE;
     int64_t k_begin, k_end;
     double *out;
     if (row_off) {
@@ -105,24 +117,34 @@ k_gram(const double *__restrict__ A, int64_t lda, int ma, const double *__restri
 
 // S[a][b] (complex, ld lds) = sum over splits (fixed order) of the real Gram,
 // folded; grid.y = realisation in a batch (S advanced by s_stride, part by
-// splits * ma * nb).
+// splits * ma * nb).  herm: an entry whose real tile lies below the diagonal
+// is the conjugate of its mirror, S[a][b] = conj(S[b][a]).
 __global__ void k_gram_fold(const double *part, int splits, int ma, int nb, double2 *S, int64_t lds,
-                            int64_t s_stride) {
+                            int64_t s_stride, int herm) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int na = ma / 2, nbc = nb / 2;
     if (e >= na * nbc) return;
     part += (int64_t)blockIdx.y * splits * ma * nb;
     S += (int64_t)blockIdx.y * s_stride;
-    int a = e / nbc, b = e % nbc;
+    const int a = e / nbc, b = e % nbc;
+    const bool mirror = herm && (2 * a) / GR_TILE > (2 * b) / GR_TILE;
+    const int r = mirror ? b : a, c = mirror ? a : b;     // the computed entry
     double g00 = 0, g11 = 0, g01 = 0, g10 = 0;
     for (int s = 0; s < splits; ++s) {
         const double *P = part + (int64_t)s * ma * nb;
-        g00 += P[(int64_t)(2 * a) * nb + 2 * b];
-        g11 += P[(int64_t)(2 * a + 1) * nb + 2 * b + 1];
-        g01 += P[(int64_t)(2 * a) * nb + 2 * b + 1];
-        g10 += P[(int64_t)(2 * a + 1) * nb + 2 * b];
+        g00 += P[(int64_t)(2 * r) * nb + 2 * c];
+        g11 += P[(int64_t)(2 * r + 1) * nb + 2 * c + 1];
+        g01 += P[(int64_t)(2 * r) * nb + 2 * c + 1];
+        g10 += P[(int64_t)(2 * r + 1) * nb + 2 * c];
     }
-    S[(int64_t)a * lds + b] = make_double2(g00 + g11, g01 - g10);
+    const double im = g01 - g10;
+    S[(int64_t)a * lds + b] = make_double2(g00 + g11, mirror ? -im : im);
+}
+
+// Output tiles a Gram launch computes: all of them, or the upper triangle.
+static int gram_tiles(int ma, int nb, bool herm) {
+    const int tm = (ma + GR_TILE - 1) / GR_TILE, tn = (nb + GR_TILE - 1) / GR_TILE;
+    return herm ? tn * (tn + 1) / 2 : tm * tn;
 }
 
 // K-splits of a Gram: about GRAM_TARGET_CTAS CTAs in total, at least 4 slabs of
@@ -141,19 +163,20 @@ size_t gram_workspace(int64_t K, int na, int nbc) {
 }
 
 cfd_status gram(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nbc, int64_t K,
-                double2 *S, int64_t lds, double *work, cudaStream_t stream) {
+                double2 *S, int64_t lds, double *work, cudaStream_t stream, bool herm) {
     int ma = 2 * na, nb = 2 * nbc;
-    int splits = gram_splits(K, ma, nb);
+    if (herm && ma != nb) return fail(CFD_ERR_INTERNAL, "Hermitian Gram of non-square shape");
+    int splits = gram_splits(K, ma, nb);     // the workspace holds this many partials
     int64_t rps = ((K + splits - 1) / splits + GR_KS - 1) / GR_KS * GR_KS;
     splits = (int)((K + rps - 1) / rps);
-    int tiles = ((ma + GR_TILE - 1) / GR_TILE) * ((nb + GR_TILE - 1) / GR_TILE);
-    dim3 grid(tiles, std::max(splits, 1));
+    dim3 grid(gram_tiles(ma, nb, herm), std::max(splits, 1));
     k_gram<<<grid, GR_THREADS, 0, stream>>>(reinterpret_cast<const double *>(X), 2 * ldx, ma,
-                                           reinterpret_cast<const double *>(Y), 2 * ldy, nb, K, rps, work, nullptr);
+                                           reinterpret_cast<const double *>(Y), 2 * ldy, nb, K, rps, work, nullptr,
+                                           herm ? 1 : 0);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     int n = na * nbc;
-    k_gram_fold<<<(n + 255) / 256, 256, 0, stream>>>(work, std::max(splits, 1), ma, nb, S, lds, 0);
+    k_gram_fold<<<(n + 255) / 256, 256, 0, stream>>>(work, std::max(splits, 1), ma, nb, S, lds, 0, herm ? 1 : 0);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;
@@ -173,18 +196,18 @@ size_t gram_batched_workspace(int R, int na, int nbc) {
 
 cfd_status gram_batched(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nbc,
                         const int64_t *row_off_dev, int R, double2 *S, int64_t lds, int64_t s_stride, double *work,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, bool herm) {
     int ma = 2 * na, nb = 2 * nbc;
+    if (herm && ma != nb) return fail(CFD_ERR_INTERNAL, "Hermitian Gram of non-square shape");
     int splits = gram_batched_splits(R, ma, nb);
-    int tiles = ((ma + GR_TILE - 1) / GR_TILE) * ((nb + GR_TILE - 1) / GR_TILE);
-    dim3 grid(tiles, splits, R);
+    dim3 grid(gram_tiles(ma, nb, herm), splits, R);
     k_gram<<<grid, GR_THREADS, 0, stream>>>(reinterpret_cast<const double *>(X), 2 * ldx, ma,
                                            reinterpret_cast<const double *>(Y), 2 * ldy, nb, 0, 0, work,
-                                           row_off_dev);
+                                           row_off_dev, herm ? 1 : 0);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     int n = na * nbc;
-    k_gram_fold<<<dim3((n + 255) / 256, R), 256, 0, stream>>>(work, splits, ma, nb, S, lds, s_stride);
+    k_gram_fold<<<dim3((n + 255) / 256, R), 256, 0, stream>>>(work, splits, ma, nb, S, lds, s_stride, herm ? 1 : 0);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;

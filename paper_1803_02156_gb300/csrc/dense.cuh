@@ -13,9 +13,13 @@ constexpr int DENSE_BATCH_MAX_N = 64;   // widest block per realisation in batch
 
 // S (na x nb complex, ld lds) = X^H Y for N x na and N x nb blocks (unit column
 // stride, ld in complex elements).  Deterministic (fixed-order split reduction).
+// herm (na == nb, S Hermitian: X^H X, or X^H H X with Y = H X): only the
+// output tiles on and above the diagonal are computed (about half the flops
+// for n >= 64) and S below them is the conjugate mirror, as LAPACK's
+// Hermitian eigensolvers read one triangle.
 size_t gram_workspace(int64_t K, int na, int nb);
 cfd_status gram(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nb, int64_t K,
-                double2 *S, int64_t lds, double *work, cudaStream_t stream);
+                double2 *S, int64_t lds, double *work, cudaStream_t stream, bool herm = false);
 
 // X[:, 0:n_out] <- X[:, 0:n_in] M (M n_in x n_out complex, ld ldm), in place, n_out <= n_in.
 size_t project_workspace(int n_in, int n_out);
@@ -39,7 +43,7 @@ cfd_status resid_norms(const double2 *Z, int64_t ldz, const double2 *X, int64_t 
 size_t gram_batched_workspace(int R, int na, int nb);
 cfd_status gram_batched(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nb,
                         const int64_t *row_off_dev, int R, double2 *S, int64_t lds, int64_t s_stride, double *work,
-                        cudaStream_t stream);
+                        cudaStream_t stream, bool herm = false);
 size_t project_batched_workspace(int R, int n);
 cfd_status project_batched(double2 *X, int64_t ldx, int64_t n_rows, int n, const double2 *M, int64_t ldm,
                            int64_t m_stride, const int64_t *row_off_dev, int R, double *work, cudaStream_t stream);

@@ -70,7 +70,7 @@ cfd_status svqb_pass(double2 *X, int64_t ldx, int64_t N, int n, double tau, void
     size_t ew_bytes = eigh_workspace(n);
     void *ew = c.take<char>(ew_bytes);
     if (!c.fits()) return fail(CFD_ERR_OOM, "orthogonalisation workspace too small");
-    CFD_TRY(gram(X, ldx, n, X, ldx, n, N, S, n, gw, stream));
+    CFD_TRY(gram(X, ldx, n, X, ldx, n, N, S, n, gw, stream, true));
     k_svqb_scale<<<(n * n + 255) / 256, 256, 0, stream>>>(S, n, d);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
@@ -188,7 +188,7 @@ cfd_status rayleigh_ritz_impl(const cfd_matrix *H, const cfd_block &X, double *e
     double2 *Xp = static_cast<double2 *>(X.ptr);
     CFD_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), stream));
     CFD_TRY(spmmv_block(H, Xp, X.ld, Z, n, n, partial, ticket, nullptr, stream));   // no moments needed
-    CFD_TRY(gram(Xp, X.ld, n, Z, n, n, N, G, n, gw, stream));
+    CFD_TRY(gram(Xp, X.ld, n, Z, n, n, N, G, n, gw, stream, true));   // X^H H X is Hermitian
     CFD_TRY(eigh(G, n, n, evals, Y, n, ew, ewb, stream, nullptr));
     CFD_TRY(project_inplace(Xp, X.ld, N, n, Y, n, n, pw, stream));
     CFD_TRY(project_inplace(Z, n, N, n, Y, n, n, pw, stream));

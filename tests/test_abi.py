@@ -79,3 +79,52 @@ def test_filter_argument_validation_on_host(L):
     X64 = b.cfd_block(ptr=1 << 20, n_rows=2048, ld=32, n_cols=32, prec=1)
     assert call(X=X64) == 1                                     # c128 matrix with c64 block
     assert b"n_b" in L.cfd_last_error() or len(L.cfd_last_error()) > 0
+
+
+def _fake_matrix(b, n_rows=2048, nnz=25600, C=32):
+    return b.cfd_matrix(n_rows=n_rows, nnz=nnz, n_chunks=(n_rows + C - 1) // C, n_slots=nnz, C=C, sigma=1, prec=0,
+                        val=4096, col=4096, chunk_ptr=4096, chunk_len=4096, perm=None)
+
+
+def test_filter_options_validated_on_host(L):
+    """Kernel options out of range are rejected before any GPU work."""
+    from paper_1803_02156_gb300 import binding as b
+    m = _fake_matrix(b)
+    X = b.cfd_block(ptr=1 << 20, n_rows=2048, ld=32, n_cols=32, prec=0)
+
+    def call(**kw):
+        o = b.cfd_filter_opts(**kw)
+        return L.cfd_filter_ex(ctypes.byref(m), -9.0, 9.0, -0.5, 0.5, 20, X, 32, ctypes.c_void_p(1 << 24), 1 << 40,
+                               None, ctypes.byref(o), None)
+
+    assert call(gather=5) == 1
+    assert call(gather=12) == 1
+    assert call(staged=3) == 1
+    assert call(grid_cap=-1) == 1
+
+
+def test_filter_workspace_holds_prepared_values(L):
+    """The filter workspace holds the two N x n_b recurrence blocks and the
+    matrix values prepared as 2 alpha (H - beta), 13 per row (the matrices
+    this library builds), and grows with N, n_b and n_p."""
+    from paper_1803_02156_gb300 import binding as b
+    for prec, s in ((0, 16), (1, 8)):
+        for N, n_b in ((2048, 32), (524288, 32), (16000000, 64)):
+            ws = L.cfd_filter_workspace(N, 4 * n_b, n_b, 100, prec, prec)
+            assert ws >= 2 * N * n_b * s + 13 * N * s
+            assert L.cfd_filter_workspace(N + 4096, 4 * n_b, n_b, 100, prec, prec) > ws
+            assert L.cfd_filter_workspace(N, 4 * n_b, n_b, 1000, prec, prec) > ws
+    # mixed precision (complex-float matrix, complex-double block) also holds the narrowed block
+    assert L.cfd_filter_workspace(2048, 64, 32, 100, 1, 0) > L.cfd_filter_workspace(2048, 64, 32, 100, 1, 1)
+
+
+def test_noalloc_rejects_oversize_on_host(L):
+    """A problem whose workspace exceeds the static scratch is rejected with
+    CFD_ERR_ARG before the library touches a GPU."""
+    from paper_1803_02156_gb300 import binding as b
+    N = 4 * 64 * 64 * 32
+    m = _fake_matrix(b, n_rows=N, nnz=13 * N)
+    X = b.cfd_block(ptr=1 << 20, n_rows=N, ld=32, n_cols=32, prec=0)
+    st = L.cfd_filter_noalloc(ctypes.byref(m), -9.0, 9.0, -0.5, 0.5, 20, X, 32, None, None)
+    assert st == 1
+    assert b"static scratch" in L.cfd_last_error()
