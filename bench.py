@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg (profiling runs)")
+    ap.add_argument("--no-single-core", action="store_true",
+                    help="reference arm: skip the extra one-thread oracle sample")
     ap.add_argument("--tte", action="store_true", help="also time cfd_solve to n_t eigenpairs, fp64 vs mixed")
     ap.add_argument("--tte-workload", default=None, choices=sorted(workloads.ALL),
                     help="tte mode: the workload whose time to eigenpairs is measured (default: the 64x64x32 one)")
@@ -180,13 +182,25 @@ def run_reference(a):
         t_all += dt
     value = statistics.median(vals)
     sample = "%d fused steps of one n_b=%d block of %s (CPU oracle, fp64), per bench step" % (steps, a.n_b, w.name)
+    single = None
+    if not a.no_single_core and cores > 1:
+        # the same oracle on one thread, in a child process (OpenMP reads the
+        # thread count at start-up), on a shorter sample
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1",
+                            "--warmup", "0", "--cpu-sample-steps", "10", "--no-single-core"],
+                           env=dict(os.environ, OMP_NUM_THREADS="1"), capture_output=True, text=True)
+        try:
+            single = {"value": json.loads(r.stdout.strip().splitlines()[-1])["value"], "unit": UNIT, "cores": 1,
+                      "sample": "10 fused steps of one n_b=%d block" % a.n_b}
+        except (ValueError, IndexError, KeyError):
+            single = None
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * t_all / max(a.steps, 1), 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-           "data": "synthetic", "config": {"workload": w.name, "n_s": w.n_s, "n_b": a.n_b, "n_p": steps,
-                                           "lattice": list(w.lattice)},
+           "data": "synthetic", "config": {"workload": w.name, "lattice": list(w.lattice), "N": w.N, "nnz": w.nnz,
+                                           "n_s": w.n_s, "n_b": a.n_b, "n_p": w.n_p, "oracle_steps_per_sample": steps},
            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "single_core": single},
            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
