@@ -191,9 +191,10 @@ cfd_status cfd_solve_batched(const cfd_matrix *H, const cfd_matrix *H_low, const
     const int nn = n * n;
     double tf = 0, to = 0, tr = 0;
     for (int r = 0; r < R; ++r) res[r].rank_min = n;
+    PhaseEvents ev;
+    CFD_CUDA(ev.create());
+    cudaEvent_t *e = ev.e;
     for (int it = 1; it <= p->max_iter; ++it) {
-        cudaEvent_t e[4];
-        for (auto &x : e) cudaEventCreate(&x);
         cudaEventRecord(e[0], stream);
         CFD_TRY(filter_batched_impl(low ? H_low : H, chunk_rid, R, d_win, p->n_p, X, p->n_b, 0, 0, big, ws.big,
                                     stream));
@@ -228,11 +229,7 @@ cfd_status cfd_solve_batched(const cfd_matrix *H, const cfd_matrix *H_low, const
         CFD_CUDA(cudaMemcpyAsync(&dev_status, big, sizeof(int), cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaStreamSynchronize(stream));
         if (dev_status == CFD_ERR_TIMEOUT) return fail(CFD_ERR_TIMEOUT, "a bounded device-side wait expired");
-        float a = 0, b = 0, c = 0;
-        cudaEventElapsedTime(&a, e[0], e[1]);
-        cudaEventElapsedTime(&b, e[1], e[2]);
-        cudaEventElapsedTime(&c, e[2], e[3]);
-        for (auto &x : e) cudaEventDestroy(x);
+        const float a = ev.ms(0, 1), b = ev.ms(1, 2), c = ev.ms(2, 3);
         tf += a * 1e-3;
         to += b * 1e-3;
         tr += c * 1e-3;

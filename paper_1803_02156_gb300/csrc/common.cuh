@@ -48,6 +48,31 @@ inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Bump allocator over a caller-provided scratch buffer (256-byte aligned
 // sub-buffers).  Used to carve workspaces; never allocates.
+// CUDA events timing the phases of a solve iteration, created once and
+// destroyed on every exit path (error returns included).
+struct PhaseEvents {
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaError_t create() {
+        for (auto &x : e) {
+            cudaError_t st = cudaEventCreate(&x);
+            if (st != cudaSuccess) return st;
+        }
+        return cudaSuccess;
+    }
+    float ms(int a, int b) const {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e[a], e[b]);
+        return t;
+    }
+    PhaseEvents() = default;
+    PhaseEvents(const PhaseEvents &) = delete;
+    PhaseEvents &operator=(const PhaseEvents &) = delete;
+    ~PhaseEvents() {
+        for (auto x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
 struct Carve {
     char *base;
     size_t cap, off = 0;

@@ -114,9 +114,10 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
     tr.start(p->n_t, mixed);
     const double switch_tol = p->switch_tol > 0 ? p->switch_tol : 1e-4;
     res->rank_min = n;
+    PhaseEvents ev;
+    CFD_CUDA(ev.create());
     for (int it = 1; it <= p->max_iter; ++it) {
-        cudaEvent_t e0, e1, e2, e3;
-        cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); cudaEventCreate(&e3);
+        cudaEvent_t e0 = ev.e[0], e1 = ev.e[1], e2 = ev.e[2], e3 = ev.e[3];
         cudaEventRecord(e0, stream);
         CFD_TRY(filter_impl(tr.low ? H_low : H, lmin, lmax, p->lam_l, p->lam_r, p->n_p, X, p->n_b, 0, 0, scratch,
                             scratch_bytes, nullptr, stream));
@@ -134,11 +135,7 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
         CFD_CUDA(cudaMemcpyAsync(&dev_status, scratch, sizeof(int), cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaStreamSynchronize(stream));
         if (dev_status == CFD_ERR_TIMEOUT) return fail(CFD_ERR_TIMEOUT, "a bounded device-side wait expired");
-        float a = 0, b = 0, c = 0;
-        cudaEventElapsedTime(&a, e0, e1);
-        cudaEventElapsedTime(&b, e1, e2);
-        cudaEventElapsedTime(&c, e2, e3);
-        cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); cudaEventDestroy(e3);
+        const float a = ev.ms(0, 1), b = ev.ms(1, 2), c = ev.ms(2, 3);
         res->t_filter += a * 1e-3;
         res->t_orth += b * 1e-3;
         res->t_rr += c * 1e-3;
