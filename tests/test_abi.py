@@ -128,3 +128,16 @@ def test_noalloc_rejects_oversize_on_host(L):
     st = L.cfd_filter_noalloc(ctypes.byref(m), -9.0, 9.0, -0.5, 0.5, 20, X, 32, None, None)
     assert st == 1
     assert b"static scratch" in L.cfd_last_error()
+
+
+def test_sell_layout_has_no_padding_on_the_benchmark_lattices(L):
+    """SELL-C-sigma with C = 32: chunks of 8 sites never straddle a z-plane
+    when Nx Ny is a multiple of 8, so every slot holds a nonzero (packed or
+    complex values); uneven lattices pad only the chunks that straddle."""
+    from paper_1803_02156_gb300 import binding as b, workloads
+    for w in (workloads.SMALL, workloads.MEDIUM, workloads.LARGE, workloads.MIXED):
+        for prec in ("c128", "c128p", "c64p"):
+            s = b.cfd_matrix_query_size(b.topi_params(*w.lattice), 32, 1, prec)
+            assert s.n_slots == s.nnz == w.nnz
+    s = b.cfd_matrix_query_size(b.topi_params(37, 26, 17), 32, 1, "c64p")
+    assert s.nnz < s.n_slots < 1.001 * s.nnz
