@@ -247,6 +247,12 @@ size_t cfd_filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, in
  * the two seed steps) via T_k T_l = (T_{k+l} + T_{|k-l|}) / 2.  The
  * reductions are deterministic (fixed order).
  *
+ * Spectral-bounds guard: with moments requested, a moment larger than mu_0
+ * by more than 1% (an eigenvalue of H outside [lmin, lmax] makes them grow
+ * like cosh(m arccosh |lambda~|)) records CFD_ERR_BOUNDS in the workspace
+ * status, reported by cfd_workspace_status; the call itself stays
+ * asynchronous.
+ *
  * work: device scratch of cfd_filter_workspace(...) bytes.  n_b must divide
  * n_s and be one of 8, 16, 32, 64.  Asynchronous.
  * Errors: CFD_ERR_ARG (sizes, window, precision pair, alignment),
@@ -400,9 +406,11 @@ cfd_status cfd_filter_batched(const cfd_matrix *H, const int32_t *chunk_rid, int
 
 /*
  * Device-side status of a filter workspace (cfd_filter, cfd_filter_ex,
- * cfd_filter_batched): the staged kernels bound every wait on their TMA
- * copies and record CFD_ERR_TIMEOUT here if one expires.  Synchronises
- * `stream`; returns CFD_OK or the recorded status.
+ * cfd_filter_batched, cfd_kpm_moments, cfd_filter_unfused): the staged
+ * kernels bound every wait on their TMA copies and record CFD_ERR_TIMEOUT
+ * here if one expires; with moments requested the spectral-bounds guard
+ * records CFD_ERR_BOUNDS.  Synchronises `stream`; returns CFD_OK or the
+ * recorded status.
  */
 cfd_status cfd_workspace_status(const void *work, cudaStream_t stream);
 

@@ -167,12 +167,31 @@ __global__ void k_moments(const double *raw, int n_p, int nb, double *mu, int64_
     mu[(int64_t)j * ld_mu + m] = v;
 }
 
-cfd_status launch_moments(const double *raw, int n_p, int nb, double *mu, int64_t ld_mu,
+// Guard on the spectral bounds: with every eigenvalue of H~ in [-1, 1],
+// |mu_m| = |sum_i |v_i^H x|^2 T_m(lambda~_i)| <= mu_0 for every m; an
+// eigenvalue outside makes the moments grow like cosh(m arccosh |lambda~|).
+// A moment above mu_0 by more than 1% (far beyond the rounding of either
+// precision), or not finite, records CFD_ERR_BOUNDS in *status.
+__global__ void k_check_moments(const double *mu, int nb, int n_mom, int64_t ld_mu, int *status) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nb * n_mom) return;
+    const int j = (int)(e / n_mom), m = (int)(e % n_mom);
+    const double mu0 = mu[(int64_t)j * ld_mu], v = mu[(int64_t)j * ld_mu + m];
+    if (!(fabs(v) <= 1.01 * fabs(mu0)))            // also true for NaN
+        atomicCAS(status, 0, (int)CFD_ERR_BOUNDS);
+}
+
+cfd_status launch_moments(const double *raw, int n_p, int nb, double *mu, int64_t ld_mu, int *status,
                           cudaStream_t stream) {
     int64_t n = (int64_t)nb * 2 * n_p;
     k_moments<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(raw, n_p, nb, mu, ld_mu);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
+    if (status) {
+        k_check_moments<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(mu, nb, 2 * n_p, ld_mu, status);
+        CFD_COUNT_LAUNCH();
+        CFD_LAUNCH_CHECK();
+    }
     return CFD_OK;
 }
 
@@ -333,7 +352,8 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
                 CFD_TRY(launch_step<T>(STEP_GENERAL, n_b, vpt, A, P.grid_cap, stream));
             }
             if (moments)
-                CFD_TRY(launch_moments(ws.raw, n_p, n_b, moments + (int64_t)b * n_b * 2 * n_p, 2 * n_p, stream));
+                CFD_TRY(launch_moments(ws.raw, n_p, n_b, moments + (int64_t)b * n_b * 2 * n_p, 2 * n_p, ws.status,
+                                       stream));
         }
         if (mixed)
             CFD_TRY(launch_widen(static_cast<const float2 *>(ws.xn), n_b, reinterpret_cast<double2 *>(xsrc),
@@ -474,7 +494,7 @@ cfd_status kpm_impl(const cfd_matrix *H, double lmin, double lmax, int n_p, cons
                 CFD_TRY(launch_step<float>(STEP_GENERAL, n_b, vpt, A, 0, stream));
             }
         }
-        CFD_TRY(launch_moments(ws.raw, n_p, n_b, mu, 2 * n_p, stream));
+        CFD_TRY(launch_moments(ws.raw, n_p, n_b, mu, 2 * n_p, ws.status, stream));
     }
     return CFD_OK;
 }
@@ -575,6 +595,8 @@ cfd_status cfd_workspace_status(const void *work, cudaStream_t stream) {
     CFD_CUDA(cudaMemcpyAsync(&st, work, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CFD_CUDA(cudaStreamSynchronize(stream));
     if (st == CFD_ERR_TIMEOUT) return fail(CFD_ERR_TIMEOUT, "a bounded device-side wait expired");
+    if (st == CFD_ERR_BOUNDS)
+        return fail(CFD_ERR_BOUNDS, "a Chebyshev moment exceeded mu_0: [lmin, lmax] does not contain the spectrum");
     if (st != 0) return fail(CFD_ERR_INTERNAL, "device status %d", st);
     return CFD_OK;
 }

@@ -117,7 +117,9 @@ cfd_status launch_filter_coeffs(double alpha, double beta, double lam_l, double 
 cfd_status launch_prepare_values(const cfd_matrix *H, double alpha, double beta, const int32_t *chunk_rid,
                                  const double *rcoef, int64_t rcoef_ld, void *out, size_t out_bytes,
                                  cudaStream_t stream);
-cfd_status launch_moments(const double *raw, int n_p, int nb, double *mu, int64_t ld_mu,
+// raw dots -> KPM moments; with status set, also the spectral-bounds guard
+// (CFD_ERR_BOUNDS recorded when a moment exceeds mu_0).
+cfd_status launch_moments(const double *raw, int n_p, int nb, double *mu, int64_t ld_mu, int *status,
                           cudaStream_t stream);
 cfd_status launch_narrow(const double2 *src, int64_t lds, float2 *dst, int64_t ldd, int64_t n_rows,
                          int nb, cudaStream_t stream);

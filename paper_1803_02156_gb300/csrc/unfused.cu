@@ -192,7 +192,7 @@ cfd_status run_unfused(const cfd_matrix *H, double alpha, double beta, int n_p, 
             }
         }
         if (moments)
-            CFD_TRY(launch_moments(raw, n_p, n_b, moments + (int64_t)b * n_b * 2 * n_p, 2 * n_p, stream));
+            CFD_TRY(launch_moments(raw, n_p, n_b, moments + (int64_t)b * n_b * 2 * n_p, 2 * n_p, ws.f.status, stream));
         if (mixed)
             CFD_TRY(launch_widen(static_cast<const float2 *>(ws.f.xn), n_b, reinterpret_cast<double2 *>(xsrc),
                                  X.ld, N, n_b, stream));

@@ -350,3 +350,24 @@ def test_fixed_chunk_kernel_parity_ragged(b):
     assert np.linalg.norm(Xg.cpu().numpy() - Y) / np.linalg.norm(Y) < TOL_C128
     muref = oracle.kpm_moments(dots)
     assert np.max(np.abs(mu.cpu().numpy() - muref)) / np.max(np.abs(muref)) < TOL_C128
+
+
+@pytest.mark.parametrize("prec", ["c128p", "c64p"])
+def test_bounds_guard_reports_bad_bounds(b, prec):
+    """Spectral bounds that cut the spectrum (here [-2, 2] against |lambda| up
+    to about 8.5) make the Chebyshev moments grow; the filter records
+    CFD_ERR_BOUNDS in its workspace status.  Correct bounds leave it clear."""
+    import torch
+    dt = torch.complex128 if prec.startswith("c128") else torch.complex64
+    H = b.cfd_build_matrix(b.topi_params(8, 8, 4), 32, 1, prec)
+    ws = b.cfd_filter_workspace(H.N, 16, 16, 40, prec, prec)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    X0 = torch.from_numpy(inputs.gaussian_block(H.N, 16, seed=14)).to(dt).cuda()
+    X = X0.clone()
+    b.cfd_filter(H, -8.6, 8.6, -0.5, 0.5, 40, X, 16, moments=True, work=work)
+    b.cfd_workspace_status(work)                       # clear with bounds that contain the spectrum
+    X = X0.clone()
+    b.cfd_filter(H, -2.0, 2.0, -0.5, 0.5, 40, X, 16, moments=True, work=work)
+    with pytest.raises(b.CfdError) as e:
+        b.cfd_workspace_status(work)
+    assert e.value.status == 4                         # CFD_ERR_BOUNDS
