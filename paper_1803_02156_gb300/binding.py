@@ -394,7 +394,8 @@ def cfd_filter_host(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, wor
 
 
 def cfd_workspace_status(work, stream=None):
-    """Device status of a filter workspace (raises CfdError on a recorded timeout)."""
+    """Device status of a filter workspace: raises CfdError on a recorded timeout
+    (CFD_ERR_TIMEOUT) or a moment that exceeded mu_0 (CFD_ERR_BOUNDS)."""
     _check(lib().cfd_workspace_status(_ptr(work), _stream(stream)))
 
 
