@@ -367,3 +367,17 @@ def test_library_kpm_functions_match_oracle():
     lo, hi = b.cfd_kpm_window(mu, H.N, -8.6, 8.6, 0.0, 40.0)
     assert abs(oracle.kpm_count(mu, H.N, -8.6, 8.6, lo, hi) - 40.0) < 1e-6
     assert abs(lo + hi) < 1e-12
+
+
+def test_fma_pipe_flop_model_counts_the_step():
+    """The ALU roofline's flop count tallies the fused step's fp64 FMAs per row
+    and vector at 13 stored entries: packed values 2 per entry (26), shift /
+    scale / subtraction 4, X update 2, two dots 4 = 36 FMAs (72 flops); with
+    the prepared values of 2 alpha (H - beta) the 4 for the map vanish (32);
+    complex values cost 4 FMAs per entry."""
+    from paper_1803_02156_gb300 import model
+    assert model.step_fma_flops(1, 13, 1, packed=True) == 2 * 36
+    assert model.step_fma_flops(1, 13, 1, packed=True, prepared=True) == 2 * 32
+    assert model.step_fma_flops(1, 13, 1, packed=False) == 2 * (13 * 4 + 10)
+    # scales with the rows and the block width, the matrix term with nnz
+    assert model.step_fma_flops(524288, 6750208, 32, packed=True, prepared=True) == (4 * 6750208 + 12 * 524288) * 32
