@@ -1,14 +1,19 @@
 #!/usr/bin/env python
-"""ChebFD benchmark on the 64x64x32 topological-insulator lattice
-(N = 524288, complex128, n_s = 128, n_b = 32, n_p = 1000, SELL-C-sigma C = 32,
-window from the KPM estimate holding n_t = 64 states).
+"""ChebFD benchmark: the fused block polynomial filter on the 200x200x100
+topological-insulator lattice (N = 16,000,000, complex128, n_s = 256 in
+subspace blocks of n_b = 32, SELL-C-sigma C = 32), and time to eigenpairs,
+fp64 against the mixed-precision policy, on the 128x128x64 lattice.
 
-One step = one ChebFD iteration: the full filter (n_s / n_b blocks of n_p
-fused steps, with moments), SVQB orthogonalisation and Rayleigh-Ritz.  The
-metric is the filter's minimum-traffic bytes per second of the whole step.
-Prints one JSON line.  --impl reference times the CPU oracle on a bounded
-sample of the same workload.  Under torchrun every rank works on its own
-disorder realisation (independent problems, no data-path collective).
+One step = one subspace block of n_b = 32 vectors filtered with n_p = 100
+fused steps (with moments), through cfd_filter; step k filters block
+k mod 8 of the N x 256 search space in place.  The metric is the filter's
+minimum-traffic bytes per second (nnz (s + 4) + 5 N n_b s bytes per fused
+step).  Prints one JSON line, which also carries the time-to-eigenpairs
+comparison (run once after the timed region).  --impl reference times the CPU
+oracle on a bounded sample of the same workload.  Under torchrun every rank
+works on its own disorder realisation (independent problems, no data-path
+collective).  --mode iteration is the whole ChebFD iteration (filter, SVQB,
+Rayleigh-Ritz) on the 64x64x32 lattice.
 """
 import argparse
 import json
@@ -26,14 +31,51 @@ from paper_1803_02156_gb300 import model, workloads  # noqa: E402
 
 METRIC = "fused filter SpMMV GB/s"
 UNIT = "GB/s"
-WORKLOAD = workloads.MEDIUM
+WORKLOAD = workloads.MEDIUM          # --mode iteration
+LARGE = workloads.LARGE              # the default filter workload
+TTE_WORKLOAD = workloads.MIXED       # time to eigenpairs, fp64 vs mixed
+LARGE_WINDOW = (-0.3, 0.3)           # search interval of the large instance (does not change the filter's work)
 BOUNDS = (-8.6, 8.6)          # contains the Gershgorin interval [-8.5, 8.5] of the gamma = 1 lattice
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# general step on this workload at n_b = 32, from one ncu capture of each
-# kernel as it stands: (filter precision, n_b, value storage) -> bytes.
-PROFILED_TRAFFIC = {("c128", 32, "packed"): 1.559e9, ("c64", 32, "packed"): 0.681e9}
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def source_digest(paths):
+    """First 16 hex digits of the SHA-256 of the concatenated source files."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, n_b, N):
+    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+    `kernel` at block width n_b, scaled to N rows, from the committed ncu
+    summaries: a line 'traffic-record: kernel=K n_b=B N=R bytes=T
+    sources=a,b digest=D' in profiles/*.md.  The record counts only while the
+    digest of its source files equals the digest of those files now (a kernel
+    changed since the capture gives None).  The per-launch traffic of the step
+    is per row (matrix row + n_b block entries), so it scales with N."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
+        with open(path) as f:
+            for line in f:
+                line = line.strip().strip("`")
+                if not line.startswith("traffic-record:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                if kv.get("kernel") != kernel or int(kv.get("n_b", -1)) != n_b:
+                    continue
+                try:
+                    if source_digest(kv["sources"].split(",")) != kv["digest"]:
+                        continue
+                except (OSError, KeyError):
+                    continue
+                return float(kv["bytes"]) * N / float(kv["N"]), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def measured_hbm_gbs():
@@ -51,30 +93,39 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--n-b", type=int, default=WORKLOAD.n_b)
-    ap.add_argument("--n-p", type=int, default=WORKLOAD.n_p)
+    ap.add_argument("--n-b", type=int, default=None, help="subspace block width (default: the workload's)")
+    ap.add_argument("--n-p", type=int, default=None, help="filter degree (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end leg (0: --steps)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg (profiling runs)")
     ap.add_argument("--no-single-core", action="store_true",
                     help="reference arm: skip the extra one-thread oracle sample")
-    ap.add_argument("--tte", action="store_true", help="also time cfd_solve to n_t eigenpairs, fp64 vs mixed")
+    ap.add_argument("--no-tte", action="store_true",
+                    help="filter mode: skip the time-to-eigenpairs comparison after the timed region")
+    ap.add_argument("--tte", action="store_true", help="iteration mode: also time cfd_solve, fp64 vs mixed")
     ap.add_argument("--tte-workload", default=None, choices=sorted(workloads.ALL),
-                    help="tte mode: the workload whose time to eigenpairs is measured (default: the 64x64x32 one)")
-    ap.add_argument("--mode", default="filter", choices=["filter", "batch", "fusion", "host", "sweep", "tte"],
-                    help="filter: the 64x64x32 iteration (default); batch: 64 uneven realisations, batched vs "
-                         "looped; fusion: fused step vs separate SpMMV + BLAS-1 calls; host: search space in "
-                         "host memory vs in HBM, against n_p; sweep: fused-filter throughput on the 64x64x32 "
-                         "lattice for n_b = 8..64, the 200x200x100 lattice (complex128) and the 128x128x64 "
-                         "lattice (complex64 filter on a complex128 block); tte: time to eigenpairs, fp64 vs "
-                         "mixed policy, on --tte-workload")
+                    help="the workload whose time to eigenpairs is measured (default: the 128x128x64 one)")
+    ap.add_argument("--mode", default="filter",
+                    choices=["filter", "iteration", "batch", "fusion", "host", "sweep", "tte", "peaks"],
+                    help="filter: n_b = 32 blocks of the 200x200x100 lattice at n_p = 100, plus time to "
+                         "eigenpairs (default); iteration: the 64x64x32 ChebFD iteration (filter, SVQB, "
+                         "Rayleigh-Ritz); batch: 64 uneven realisations, batched vs looped; fusion: fused step "
+                         "vs separate SpMMV + BLAS-1 calls; host: search space in host memory vs in HBM, against "
+                         "n_p; sweep: fused-filter throughput per configuration; tte: time to eigenpairs, fp64 "
+                         "vs mixed policy, on --tte-workload; peaks: measured FMA rates of the fp64 and fp32 "
+                         "pipes")
     ap.add_argument("--host-lattice", default="64x64x32", help="host mode: lattice Nx x Ny x Nz")
     ap.add_argument("--host-n-s", type=int, default=128, help="host mode: search space width")
     ap.add_argument("--realisations", type=int, default=workloads.BATCH_COUNT)
     ap.add_argument("--prec", default="c128", choices=["c128", "c64"], help="filter arithmetic")
     ap.add_argument("--storage", default="packed", choices=["packed", "complex"],
                     help="matrix values as real-or-imaginary scalars (exact for Topi) or complex pairs")
-    return ap.parse_args()
+    a = ap.parse_args()
+    w = LARGE if a.mode == "filter" else WORKLOAD
+    a.n_b = a.n_b or w.n_b
+    a.n_p = a.n_p or w.n_p
+    return a
 
 
 def dist_env():
@@ -151,13 +202,29 @@ class Clocks:
 
 # ------------------------------------------------------------ reference --
 
+_ORACLE_CACHE = {}
+
+
+def host_block(N, n_b, seed):
+    """Complex Gaussian N x n_b start block for the oracle's timing samples,
+    drawn on the host with numpy's seeded generator (values do not change the
+    oracle's work; large blocks are too slow to draw with SplitMix64 in numpy)."""
+    import numpy as np
+    z = np.random.default_rng(seed).standard_normal((N, n_b, 2))
+    return (z[..., 0] + 1j * z[..., 1]) * (0.5 ** 0.5)
+
+
 def cpu_oracle_sample(w, n_b, sample_steps, seed):
     """Time the CPU oracle's filter on one n_b block of the workload for a bounded
-    number of steps; returns (GB/s by the traffic model, seconds, threads, steps)."""
+    number of steps; returns (GB/s by the traffic model, seconds, threads, steps).
+    The CSR and the block are built once per process (untimed)."""
     import oracle
-    from paper_1803_02156_gb300 import inputs
-    H = oracle.topi_csr(*w.lattice, t=w.t, m=w.m, gamma=w.gamma, seed=seed, periodic=w.periodic)
-    X = inputs.gaussian_block(H.N, n_b, seed=w.x_seed)
+    key = (w.name, seed, n_b)
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE.clear()
+        H = oracle.topi_csr(*w.lattice, t=w.t, m=w.m, gamma=w.gamma, seed=seed, periodic=w.periodic)
+        _ORACLE_CACHE[key] = (H, host_block(H.N, n_b, w.x_seed))
+    H, X = _ORACLE_CACHE[key]
     t0 = time.perf_counter()
     oracle.chebfd_filter(H, BOUNDS[0], BOUNDS[1], -0.3, 0.3, sample_steps, X, n_b)
     dt = time.perf_counter() - t0
@@ -169,11 +236,13 @@ def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = WORKLOAD
-    steps = a.cpu_sample_steps or 150
+    large = a.mode == "filter"
+    w = LARGE if large else WORKLOAD
+    # per bench step: a bounded sample of fused steps of one n_b block (a few
+    # seconds of the C oracle on all host cores)
+    steps = a.cpu_sample_steps or (4 if large else 150)
     vals = []
-    for _ in range(a.warmup if a.warmup < 1 else 1):
-        cpu_oracle_sample(w, a.n_b, 2, w.seed)
+    cpu_oracle_sample(w, a.n_b, 2, w.seed)      # untimed: builds the CSR and the block, warms the caches
     t_all = 0.0
     cores = 1
     for _ in range(a.steps):
@@ -187,18 +256,20 @@ def run_reference(a):
         # the same oracle on one thread, in a child process (OpenMP reads the
         # thread count at start-up), on a shorter sample
         r = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1",
-                            "--warmup", "0", "--cpu-sample-steps", "10", "--no-single-core"],
+                            "--warmup", "0", "--cpu-sample-steps", "1" if large else "10", "--no-single-core",
+                            "--mode", a.mode],
                            env=dict(os.environ, OMP_NUM_THREADS="1"), capture_output=True, text=True)
         try:
             single = {"value": json.loads(r.stdout.strip().splitlines()[-1])["value"], "unit": UNIT, "cores": 1,
-                      "sample": "10 fused steps of one n_b=%d block" % a.n_b}
+                      "sample": "%d fused step(s) of one n_b=%d block" % (1 if large else 10, a.n_b)}
         except (ValueError, IndexError, KeyError):
             single = None
+    cfg = {"workload": w.name, "lattice": list(w.lattice), "N": w.N, "nnz": w.nnz, "n_s": w.n_s, "n_b": a.n_b,
+           "n_p": a.n_p, "oracle_steps_per_sample": steps}
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(1e3 * t_all / max(a.steps, 1), 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-           "data": "synthetic", "config": {"workload": w.name, "lattice": list(w.lattice), "N": w.N, "nnz": w.nnz,
-                                           "n_s": w.n_s, "n_b": a.n_b, "n_p": w.n_p, "oracle_steps_per_sample": steps},
+           "data": "synthetic", "config": cfg,
            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": sample, "single_core": single},
            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -207,8 +278,11 @@ def run_reference(a):
 
 # ---------------------------------------------------------------- ours --
 
-def setup_problem(b, w, seed, storage, H=None):
-    """Matrix, spectral bounds and the KPM window holding about n_t states (untimed setup)."""
+def setup_problem(b, w, seed, storage, H=None, with_kpm=False):
+    """Matrix, spectral bounds and the KPM window holding about n_t states
+    (untimed setup).  with_kpm: also an independent KPM count of that window
+    from 32 other random vectors (the window's count is n_t by construction
+    for the 16 vectors that chose it)."""
     import torch
     from paper_1803_02156_gb300 import inputs
     p = b.topi_params(*w.lattice, t=w.t, m=w.m, gamma=w.gamma, seed=seed, periodic=w.periodic)
@@ -222,10 +296,202 @@ def setup_problem(b, w, seed, storage, H=None):
     mu = b.cfd_filter(H, lmin, lmax, lmin, lmax, w.n_p, R, 16, moments=True).cpu().numpy()
     lam_l, lam_r = b.cfd_kpm_window(mu, H.N, lmin, lmax, 0.0, float(w.n_t))
     del R
-    return p, H, lmin, lmax, lam_l, lam_r
+    if not with_kpm:
+        return p, H, lmin, lmax, lam_l, lam_r
+    R = inputs.gaussian_block_device(H.N, 32, seed=w.x_seed + 200)
+    mu = b.cfd_kpm_moments(H, lmin, lmax, w.n_p, R, 32).cpu().numpy()
+    del R
+    return p, H, lmin, lmax, lam_l, lam_r, b.cfd_kpm_count(mu, H.N, lmin, lmax, lam_l, lam_r)
 
 
-def run_gpu(a):
+def fp64_peak(b):
+    """FP64 FMA peak: (nominal GFLOP/s from the unit count and the maximum
+    clock, measured GFLOP/s of the library's FMA probe or None)."""
+    try:
+        meas = b.cfd_probe_fma("c128", 1 << 15) / 1e9
+    except Exception:            # the probe is optional for the roofline
+        meas = None
+    return FP64_PEAK_GFLOPS, meas
+
+
+def run_filter(a):
+    """Default: n_b = 32 subspace blocks of the 200x200x100 lattice filtered at
+    n_p = 100 (Algorithm 1 on one block of Algorithm 2), one block per step."""
+    import torch
+    import torch.distributed as dist
+    from paper_1803_02156_gb300 import binding as b, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = LARGE
+    n_b, n_p, n_s = a.n_b, a.n_p, w.n_s
+    n_blocks = n_s // n_b
+    seed = replica_seed(w.seed, rank)
+    prec = a.prec
+    suffix = "p" if a.storage == "packed" else ""
+    p = b.topi_params(*w.lattice, t=w.t, m=w.m, gamma=w.gamma, seed=seed, periodic=w.periodic)
+    H = b.cfd_build_matrix(p, w.sell_C, w.sell_sigma, "c128" + suffix)
+    lmin, lmax = b.cfd_spectral_bounds(H, 40, seed=w.lanczos_seed)
+    lam_l, lam_r = LARGE_WINDOW
+    if prec != "c128":
+        del H
+        torch.cuda.empty_cache()
+        H = b.cfd_build_matrix(p, w.sell_C, w.sell_sigma, prec + suffix)
+    N, nnz = H.N, H.nnz
+    # the N x n_s search space (65.5 GB), drawn on the device from a seeded generator
+    X = inputs.gaussian_block_device(N, n_s, seed=w.x_seed + rank)
+    work = torch.empty(b.cfd_filter_workspace(N, n_s, n_b, n_p, H.prec, b.CFD_C128), dtype=torch.uint8,
+                       device="cuda")
+    mu = torch.empty(n_b, 2 * n_p, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    L = b.lib()
+    blocks = [b.block_of(X[:, k * n_b:(k + 1) * n_b]) for k in range(n_blocks)]
+
+    def filt(blk, npp=n_p):
+        b._check(L.cfd_filter(H.ref(), lmin, lmax, lam_l, lam_r, npp, blk, n_b, b._ptr(work), work.numel(),
+                              b._ptr(mu), b._stream()))
+
+    for k in range(a.warmup):
+        filt(blocks[k % n_blocks])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    n0 = b.cfd_launch_count()
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for k in range(a.steps):
+            filt(blocks[k % n_blocks])
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+    launches = b.cfd_launch_count() - n0
+    t = ev[0].elapsed_time(ev[-1]) / 1e3
+    t = max_over_ranks(t, "cuda")
+    if world > 1:
+        dist.barrier()
+    clocks = clk.summary()
+    b.cfd_workspace_status(work)         # a recorded device-side error voids the run
+
+    # per-launch time of the general fused step: a step's time less that of
+    # the same call with n_p = 2 (weights, prepared values, steps 1 and 2,
+    # moments), over its n_p - 2 general steps; CUDA events on the launch stream
+    t_steps = sorted(ev[k].elapsed_time(ev[k + 1]) / 1e3 for k in range(a.steps))
+    t_med = t_steps[len(t_steps) // 2]
+    cal = []
+    for k in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        filt(blocks[k % n_blocks], 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cal.append(e0.elapsed_time(e1) / 1e3)
+    t_fixed = sorted(cal)[1]
+    t_launch = (t_med - t_fixed) / (n_p - 2)
+
+    step_bytes = model.step_bytes(N, nnz, n_b, prec)
+    value = world * a.steps * n_p * step_bytes / t / 1e9
+    gflops = world * a.steps * n_p * model.step_flops(N, nnz, n_b) / t / 1e9
+    gbs_launch = step_bytes / t_launch / 1e9
+    hbm, hbm_src = measured_hbm_gbs()
+    if prec == "c128":
+        nominal, measured = fp64_peak(b)
+        fma = model.step_fma_flops(N, nnz, n_b, packed=(a.storage == "packed"), prepared=True)
+        achieved = fma / t_launch / 1e9
+        kname = "k_cheb_step_staged_c128"
+        traffic, tsrc = profiled_traffic(kname, n_b, N)
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(nominal, 1), "unit": "GFLOP/s",
+                "frac": round(achieved / nominal, 4), "traffic": traffic, "traffic_source": tsrc,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "measured_peak": round(measured, 1) if measured else None,
+                "frac_of_measured_peak": round(achieved / measured, 4) if measured else None,
+                "kernel": "k_cheb_step_staged<double,%d,%d,moments,%s>" % (n_b, 2 if n_b >= 16 else 1, a.storage),
+                "algorithmic": "(4 nnz + 12 N) n_b FMA-pipe flops per launch",
+                "avg_launch_ms": round(1e3 * t_launch, 4), "hbm_gbs": round(gbs_launch, 1),
+                "hbm_frac": round(gbs_launch / hbm, 4), "hbm_peak": hbm}
+    else:
+        kname = "k_cheb_step_staged_c64"
+        traffic, tsrc = profiled_traffic(kname, n_b, N)
+        roof = {"bound": "hbm", "achieved": round(gbs_launch, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(gbs_launch / hbm, 4), "traffic": traffic, "traffic_source": tsrc,
+                "peak_source": hbm_src, "kernel": "k_cheb_step_staged<float,%d,2,moments,%s>" % (n_b, a.storage),
+                "algorithmic": "nnz (8 + 4) + 5 N n_b 8 bytes per launch",
+                "avg_launch_ms": round(1e3 * t_launch, 4)}
+    roof["avg_launch_note"] = ("(median step - median n_p=2 call) / (n_p - 2), CUDA events on the launch stream; "
+                               "fixed part %.2f ms" % (1e3 * t_fixed))
+
+    e2e = None
+    if not a.no_e2e:
+        # through the C ABI with host buffers: every step copies one n_b block
+        # from pinned host memory, filters it, and reads it and its moments back
+        ke = a.e2e_steps or a.steps
+        Xb = torch.empty(N, n_b, dtype=torch.complex128, device="cuda")
+        Xh = X[:, :n_b].cpu().pin_memory()
+        Xo = torch.empty_like(Xh).pin_memory()
+        muh = torch.empty(n_b, 2 * n_p, dtype=torch.float64).pin_memory()
+        bb = b.block_of(Xb)
+        Xb.copy_(Xh, non_blocking=True)
+        filt(bb)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            Xb.copy_(Xh, non_blocking=True)
+            filt(bb)
+            Xo.copy_(Xb, non_blocking=True)
+            muh.copy_(mu, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = max_over_ranks(e0.elapsed_time(e1) / 1e3, "cuda")
+        e2e = {"value": round(world * ke * n_p * step_bytes / te / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": N * n_b * 16, "d2h_bytes_per_step": N * n_b * 16 + n_b * 2 * n_p * 8,
+               "steps": ke}
+        del Xb, Xh, Xo
+    del X, work
+    torch.cuda.empty_cache()
+
+    tte = None
+    if not a.no_tte and rank == 0:
+        tw = workloads.ALL[a.tte_workload] if a.tte_workload else TTE_WORKLOAD
+        tp, tH, tlmin, tlmax, tl, tr, kpm = setup_problem(b, tw, tw.seed, a.storage, with_kpm=True)
+        tte = time_to_eigenpairs(b, tw, tp, tH, tlmin, tlmax, tl, tr, a.storage)
+        tte["workload"] = tw.name
+        tte["kpm_count_in_window"] = round(kpm, 2)
+        del tH
+        torch.cuda.empty_cache()
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not a.no_cpu:
+            v, dt, cores, sst = cpu_oracle_sample(w, n_b, a.cpu_sample_steps or 4, seed)
+            cpu = {"value": round(v, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d fused steps of one n_b=%d block of %s, fp64 C oracle, %.1f s" % (
+                       sst, n_b, w.name, dt)}
+        out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": round(1e3 * t / a.steps, 3), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+               "config": {"workload": w.name, "lattice": list(w.lattice), "N": N, "nnz": nnz, "n_s": n_s,
+                          "n_b": n_b, "n_p": n_p, "window": list(LARGE_WINDOW),
+                          "bounds": [round(lmin, 6), round(lmax, 6)], "sell_C": w.sell_C,
+                          "sell_sigma": w.sell_sigma, "matrix_values": a.storage,
+                          "step": "one n_b block filtered with n_p fused steps and moments (block k mod %d)"
+                                  % n_blocks,
+                          "filter_precision": "fp64" if prec == "c128" else "fp32 filter on fp64 block (mixed)",
+                          "l2": "inputs larger than L2 (X %.1f GB, work blocks %.1f GB)" % (
+                              N * n_s * 16 / 1e9, 2 * N * n_b * (16 if prec == "c128" else 8) / 1e9),
+                          "parallelism": "replicas" if world > 1 else "single"},
+               "gflops": round(gflops, 2), "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+               "cpu_baseline": cpu, "e2e": e2e}
+        if tte is not None:
+            out["time_to_eigenpairs"] = tte
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_iteration(a):
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -305,14 +571,14 @@ def run_gpu(a):
         achieved = fma / t_launch / 1e9
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GFLOPS, 1),
                 "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-                "traffic": PROFILED_TRAFFIC.get((prec, n_b, a.storage)),
+                "traffic": profiled_traffic("k_cheb_step_staged_c128", n_b, N)[0],
                 "peak_source": "nominal FP64 FMA rate (152 SMs x 2/clk x 2.07 GHz)",
                 "kernel": "k_cheb_step_staged<double,%d,%d,moments,%s>" % (n_b, 2 if n_b >= 16 else 1, a.storage),
                 "avg_launch_ms": round(1e3 * t_launch, 4), "hbm_gbs": round(gbs_launch, 1),
                 "hbm_frac": round(gbs_launch / hbm, 4)}
     else:
         roof = {"bound": "hbm", "achieved": round(gbs_launch, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(gbs_launch / hbm, 4), "traffic": PROFILED_TRAFFIC.get((prec, n_b, a.storage)),
+                "frac": round(gbs_launch / hbm, 4), "traffic": profiled_traffic("k_cheb_step_staged_c64", n_b, N)[0],
                 "peak_source": hbm_src,
                 "kernel": "k_cheb_step_staged<float,%d,2,moments,%s%s>" % (
                     n_b, a.storage, ",chunk height 32" if a.storage == "packed" else ""),
@@ -340,7 +606,7 @@ def run_gpu(a):
         e2e = {"value": round(world * a.steps * filt_bytes / te / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + n_s * 8}
 
-    tte = time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a) if (a.tte and rank == 0) else None
+    tte = time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a.storage) if (a.tte and rank == 0) else None
 
     if rank == 0:
         cpu = None
@@ -374,12 +640,13 @@ def run_gpu(a):
         dist.destroy_process_group()
 
 
-def time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a):
+def time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, storage):
     """Wall time of cfd_solve to n_t eigenpairs at residual <= 1e-10 from a random
-    start block, fp64 policy vs mixed policy (fp32 filter, then fp64)."""
+    start block, fp64 policy vs mixed policy (fp32 filter, then fp64), with
+    the workload's n_p and n_b."""
     import numpy as np
     import torch
-    suffix = "p" if a.storage == "packed" else ""
+    suffix = "p" if storage == "packed" else ""
     Hl = b.cfd_build_matrix(p, w.sell_C, w.sell_sigma, "c64" + suffix)
     out = {}
     res = {}
@@ -387,15 +654,18 @@ def time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a):
         X = torch.empty(H.N, w.n_s, dtype=torch.complex128, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        th, rs, r = b.cfd_solve(H, X, lam_l, lam_r, a.n_p, a.n_b, H_low=hl, policy=pol, lmin=lmin, lmax=lmax,
+        th, rs, r = b.cfd_solve(H, X, lam_l, lam_r, w.n_p, w.n_b, H_low=hl, policy=pol, lmin=lmin, lmax=lmax,
                                 tol=1e-10, n_t=w.n_t, max_iter=30, seed=w.x_seed, raise_noconv=False)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         conv = (th >= lam_l) & (th <= lam_r) & (rs <= 1e-10)
         res[name] = np.sort(th[conv])
         out[name] = {"seconds": round(dt, 3), "iters": r.iters, "iters_fp32": r.iters_low, "n_conv": int(r.n_conv),
+                     "stop": "n_t reached" if r.n_conv >= w.n_t else "converged count stable",
                      "max_resid": float(rs[conv].max()) if conv.any() else None,
                      "t_filter": round(r.t_filter, 3), "t_orth": round(r.t_orth, 3), "t_rr": round(r.t_rr, 3)}
+        del X
+        torch.cuda.empty_cache()
     # each run may converge a pair or two the other has not reached yet (the
     # levels come in degenerate pairs): match every fp64 eigenvalue with the
     # nearest mixed one and compare the pairs both runs found
@@ -410,6 +680,11 @@ def time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a):
         out["max_eval_diff_mixed_vs_fp64"] = None
     out["speedup_mixed"] = round(out["fp64"]["seconds"] / out["mixed"]["seconds"], 3)
     out["tol"] = 1e-10
+    out["n_t"] = w.n_t
+    out["n_s"] = w.n_s
+    out["n_p"] = w.n_p
+    out["window"] = [round(lam_l, 6), round(lam_r, 6)]
+    del Hl
     return out
 
 
@@ -714,16 +989,30 @@ def run_tte(a):
     import torch
     from paper_1803_02156_gb300 import binding as b
     torch.cuda.set_device(0)
-    w = workloads.ALL[a.tte_workload] if a.tte_workload else WORKLOAD
-    a.n_p, a.n_b = w.n_p, w.n_b
-    p, H, lmin, lmax, lam_l, lam_r = setup_problem(b, w, w.seed, a.storage)
-    res = time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a)
+    w = workloads.ALL[a.tte_workload] if a.tte_workload else TTE_WORKLOAD
+    p, H, lmin, lmax, lam_l, lam_r, kpm = setup_problem(b, w, w.seed, a.storage, with_kpm=True)
+    res = time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a.storage)
+    res["kpm_count_in_window"] = round(kpm, 2)
     print(json.dumps({"metric": "time to eigenpairs, fp64 vs mixed", "unit": "s", "n_gpus": 1, "data": "synthetic",
                       "higher_is_better": False,
                       "config": {"workload": w.name, "lattice": list(w.lattice), "N": H.N, "n_s": w.n_s,
                                  "n_t": w.n_t, "n_p": w.n_p, "n_b": w.n_b, "window": [lam_l, lam_r],
                                  "bounds": [lmin, lmax]},
                       "time_to_eigenpairs": res}))
+
+
+def run_peaks(a):
+    """Measured FMA rates of the fp64 and fp32 pipes (the library's probe)."""
+    import torch
+    from paper_1803_02156_gb300 import binding as b
+    torch.cuda.set_device(0)
+    out = {}
+    for prec in ("c128", "c64"):
+        rates = [b.cfd_probe_fma(prec, 1 << 15) / 1e9 for _ in range(max(a.steps, 1))]
+        out[{"c128": "fp64", "c64": "fp32"}[prec]] = {"gflops_median": round(statistics.median(rates), 1),
+                                                       "gflops_max": round(max(rates), 1)}
+    print(json.dumps({"metric": "FMA pipe peaks", "unit": "GFLOP/s", "n_gpus": 1, "steps": a.steps,
+                      "nominal_fp64_gflops": round(FP64_PEAK_GFLOPS, 1), "results": out}))
 
 
 def main():
@@ -740,8 +1029,12 @@ def main():
         run_sweep(a)
     elif a.mode == "tte":
         run_tte(a)
+    elif a.mode == "peaks":
+        run_peaks(a)
+    elif a.mode == "iteration":
+        run_iteration(a)
     else:
-        run_gpu(a)
+        run_filter(a)
 
 
 if __name__ == "__main__":

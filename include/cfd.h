@@ -279,7 +279,13 @@ typedef struct cfd_filter_opts {
                              for that chunk height (32-bit gather offsets, where they fit); -1 the
                              generic kernel; 0 the default (compiled height for complex float,
                              generic for complex double).  Results do not depend on it. */
-    int32_t reserved[2];
+    int32_t arith;        /* complex-double filters: 0 native fp64 arithmetic (the FP64 pipe); 1 double-word
+                             arithmetic on the fp32 pipe for the general steps (n_p - 2 of n_p): every double
+                             carried as hi + lo floats (about 48 significant bits, each operation accurate to
+                             a few units of 2^-48 against 2^-53 natively), complex-double storage and memory
+                             traffic unchanged; needs packed values (CFD_PACK_RI), not with persistent.
+                             Results agree with arith 0 to that rounding, not bit for bit. */
+    int32_t reserved;
 } cfd_filter_opts;
 
 /* cfd_filter with explicit kernel options (the autotuner's knobs besides n_b,
@@ -410,7 +416,9 @@ cfd_status cfd_filter_batched(const cfd_matrix *H, const int32_t *chunk_rid, int
  * kernels bound every wait on their TMA copies and record CFD_ERR_TIMEOUT
  * here if one expires; with moments requested the spectral-bounds guard
  * records CFD_ERR_BOUNDS.  Synchronises `stream`; returns CFD_OK or the
- * recorded status.
+ * recorded status.  A timeout whose CTA also gave up waiting for its own
+ * copies in flight is reported as CFD_ERR_TIMEOUT with a message saying so:
+ * then the launch's results and the workspace contents are invalid.
  */
 cfd_status cfd_workspace_status(const void *work, cudaStream_t stream);
 
@@ -432,17 +440,30 @@ cfd_status cfd_workspace_status(const void *work, cudaStream_t stream);
  * with CFD_ERR_ARG (for complex double roughly N (32 n_b + 208) bytes <= 64 MiB, e.g. N <= 54000 at n_b = 32).
  * Nothing is allocated: no cudaMalloc/cudaFree and no allocating library call.
  *
- * The first call on a device looks up the scratch array's device address
- * (with that device current) and caches it; make that first call before any
- * stream capture.  All calls share the one array and it keeps the last
- * call's contents (what must start at zero is cleared by each call), so
- * calls that can overlap on the GPU -- on different streams, or from
- * different host threads without ordering -- race and corrupt each other;
- * serialise them on one stream.
+ * Argument errors are reported as by cfd_filter before the size check.
+ *
+ * Every call looks up the scratch array's device address with the current
+ * device current (no allocation, no stream work); the first lookup on a
+ * device may load the library's device code there, so make the first call on
+ * each device before any stream capture.  All calls share the one array and
+ * it keeps the last call's contents (what must start at zero is cleared by
+ * each call), so calls that can overlap on the GPU -- on different streams,
+ * or from different host threads without ordering -- race and corrupt each
+ * other; serialise them on one stream.  Device-side errors of the last call
+ * (a bounded wait that expired, moments that left [-mu_0, mu_0]) are recorded
+ * in the scratch and read by cfd_filter_noalloc_status.
  */
 cfd_status cfd_filter_noalloc(const cfd_matrix *H, double lmin, double lmax, double lam_l,
                               double lam_r, int n_p, cfd_block X, int n_b, double *moments,
                               cudaStream_t stream);
+
+/*
+ * Device-side status of the last cfd_filter_noalloc call on the current
+ * device, as cfd_workspace_status reports it for a caller's workspace:
+ * CFD_OK, CFD_ERR_TIMEOUT or CFD_ERR_BOUNDS.  Queue it on the stream of that
+ * call; it synchronises `stream`.  (No counterpart in the paper.)
+ */
+cfd_status cfd_filter_noalloc_status(cudaStream_t stream);
 
 
 /* ------------------------------------------------------------------------ */
@@ -529,8 +550,11 @@ cfd_status cfd_rayleigh_ritz(const cfd_matrix *H, cfd_block X, double *evals, do
 /* ------------------------------------------------------------------------ */
 
 typedef enum cfd_policy {
-    CFD_POLICY_FP64 = 0,   /* every filter application in fp64 */
-    CFD_POLICY_MIXED = 1   /* fp32 filter until it stalls, then fp64; SVQB and RR always fp64 */
+    CFD_POLICY_FP64 = 0,     /* every filter application in fp64 */
+    CFD_POLICY_MIXED = 1,    /* fp32 filter until it stalls, then fp64; SVQB and RR always fp64 */
+    CFD_POLICY_FP64_DW = 2,  /* as FP64 with the filter's general steps in double-word arithmetic on the
+                                fp32 pipe (cfd_filter_opts.arith = 1; H needs packed values) */
+    CFD_POLICY_MIXED_DW = 3  /* as MIXED with the fp64 filter phase in double-word arithmetic */
 } cfd_policy;
 
 typedef struct cfd_solve_params {
@@ -605,6 +629,27 @@ cfd_status cfd_solve_batched(const cfd_matrix *H, const cfd_matrix *H_low, const
                              const int32_t *n_t, const cfd_solve_params *p, cfd_block X, double *evals,
                              double *resid, cfd_solve_result *res, void *work, size_t work_bytes,
                              cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement helper                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Device scratch bytes of cfd_probe_fma on the current device. */
+size_t cfd_probe_fma_workspace(void);
+
+/*
+ * Measured fused multiply-add rate of the current GPU in flop/s (2 flops per
+ * FMA): CFD_C128 probes the fp64 pipe, CFD_C64 the fp32 pipe.  Each thread of
+ * a full wave of resident CTAs runs 8 independent chains of `iters` FMAs; one
+ * short untimed launch precedes the launch timed with CUDA events on
+ * `stream`.  It is the denominator of the roofline of an arithmetic-bound
+ * step (Sect. 3.4 bounds the filter by min(memory, arithmetic); the paper
+ * takes the arithmetic peak from the vendor's figure).  Synchronises
+ * `stream`.  work: cfd_probe_fma_workspace() bytes of device memory.
+ * Errors: CFD_ERR_ARG (prec, iters < 1, NULL), CFD_ERR_OOM, CFD_ERR_CUDA.
+ */
+cfd_status cfd_probe_fma(int prec, int iters, double *flops, void *work, size_t work_bytes,
+                         cudaStream_t stream);
 
 #ifdef __cplusplus
 }

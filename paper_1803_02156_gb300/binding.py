@@ -65,7 +65,7 @@ class cfd_block(ctypes.Structure):
 class cfd_filter_opts(ctypes.Structure):
     _fields_ = [("vpt", ctypes.c_int32), ("grid_cap", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("staged", ctypes.c_int32), ("gather", ctypes.c_int32),
-                ("fixed_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("fixed_chunk", ctypes.c_int32), ("arith", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class cfd_solve_params(ctypes.Structure):
@@ -83,7 +83,7 @@ class cfd_solve_result(ctypes.Structure):
                 ("t_total", ctypes.c_double)]
 
 
-CFD_POLICY_FP64, CFD_POLICY_MIXED = 0, 1
+CFD_POLICY_FP64, CFD_POLICY_MIXED, CFD_POLICY_FP64_DW, CFD_POLICY_MIXED_DW = 0, 1, 2, 3
 
 # ---------------------------------------------------------------- load --
 
@@ -177,6 +177,10 @@ _PROTOS = {
     "cfd_filter_noalloc": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block,
                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "cfd_filter_noalloc_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "cfd_probe_fma_workspace": (ctypes.c_size_t, []),
+    "cfd_probe_fma": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.c_void_p]),
 }
 
 
@@ -338,17 +342,18 @@ def cfd_filter(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=Non
 
 
 def cfd_filter_ex(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, vpt=0, grid_cap=0, moments=False, work=None,
-                  stream=None, persistent=0, staged=0, gather=0, fixed_chunk=0):
+                  stream=None, persistent=0, staged=0, gather=0, fixed_chunk=0, arith=0):
     """cfd_filter with the kernel options (vectors per thread, CTA cap, persistent
     launch, TMA staging: 1 on, -1 off, 0 default; gathers in flight per row in
     staged steps: 16 all at once, 4 groups of four, 0 default; fixed_chunk -1:
-    generic staged kernel instead of the one compiled for C = 32)."""
+    generic staged kernel instead of the one compiled for C = 32; arith 1:
+    complex-double general steps in double-word arithmetic on the fp32 pipe)."""
     blk = block_of(X)
     ws = cfd_filter_workspace(H.N, blk.n_cols, n_b, n_p, H.prec, blk.prec)
     if work is None or work.numel() < ws:
         work = _workspace(ws, X.device)
     mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=X.device) if moments else None
-    o = cfd_filter_opts(vpt, grid_cap, persistent, staged, gather, fixed_chunk)
+    o = cfd_filter_opts(vpt, grid_cap, persistent, staged, gather, fixed_chunk, arith)
     _check(lib().cfd_filter_ex(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
                                _ptr(mu), ctypes.byref(o), _stream(stream)))
     return mu
@@ -609,3 +614,17 @@ def cfd_filter_noalloc(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=None, s
     _check(lib().cfd_filter_noalloc(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(moments),
                                     _stream(stream)))
 
+
+def cfd_filter_noalloc_status(stream=None):
+    """Device status of the last cfd_filter_noalloc call on this device: raises
+    CfdError on a recorded timeout or moment growth (as cfd_workspace_status)."""
+    _check(lib().cfd_filter_noalloc_status(_stream(stream)))
+
+
+def cfd_probe_fma(prec="c128", iters=1 << 16, device="cuda", stream=None):
+    """Measured FMA rate of the current GPU in flop/s: "c128" the fp64 pipe, "c64" the fp32 pipe."""
+    work = _workspace(lib().cfd_probe_fma_workspace(), device)
+    out = ctypes.c_double()
+    _check(lib().cfd_probe_fma(_prec(prec), int(iters), ctypes.byref(out), _ptr(work), work.numel(),
+                               _stream(stream)))
+    return out.value

@@ -128,6 +128,8 @@ cfd_status cfd_solve_batched(const cfd_matrix *H, const cfd_matrix *H_low, const
     if (!p || !chunk_rid || !row_off || !row_end || !windows || !n_t || !evals || !resid || !res || !work || R < 1)
         return fail(CFD_ERR_ARG, "NULL argument");
     if (H->prec != CFD_C128) return fail(CFD_ERR_ARG, "H must be the complex-double batch");
+    if (p->policy != CFD_POLICY_FP64 && p->policy != CFD_POLICY_MIXED)
+        return fail(CFD_ERR_ARG, "the batched solve supports the FP64 and MIXED policies (got %d)", p->policy);
     const bool mixed = p->policy == CFD_POLICY_MIXED;
     if (mixed) {
         if (!H_low) return fail(CFD_ERR_ARG, "mixed policy needs the complex-float batch H_low");
@@ -228,7 +230,7 @@ cfd_status cfd_solve_batched(const cfd_matrix *H, const cfd_matrix *H_low, const
         int dev_status = 0;          // the filter workspace starts with its status word
         CFD_CUDA(cudaMemcpyAsync(&dev_status, big, sizeof(int), cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaStreamSynchronize(stream));
-        if (dev_status == CFD_ERR_TIMEOUT) return fail(CFD_ERR_TIMEOUT, "a bounded device-side wait expired");
+        if ((dev_status & 0xff) == CFD_ERR_TIMEOUT) return fail(CFD_ERR_TIMEOUT, "a bounded device-side wait expired");
         const float a = ev.ms(0, 1), b = ev.ms(1, 2), c = ev.ms(2, 3);
         tf += a * 1e-3;
         to += b * 1e-3;

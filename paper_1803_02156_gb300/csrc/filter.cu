@@ -307,7 +307,13 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
     A.gather = P.gather;
     A.fixed_chunk = P.fixed_chunk;
     A.status = ws.status;
-    if (P.staged && !P.persistent) {
+    const bool dw = std::is_same<T, double>::value && P.arith == ARITH_DW;
+    if (dw) {
+        // double-word general steps: 2 alpha (H - beta) as {hi, lo} float pairs
+        CFD_TRY(launch_prepare_values_dw(H, P.alpha, P.beta, P.chunk_rid, P.rcoef, P.rcoef_ld, ws.prep,
+                                         ws.prep_bytes, stream));
+        A.prep_val = ws.prep;
+    } else if (P.staged && !P.persistent) {
         // the staged general steps read 2 alpha (H - beta), prepared once per call
         CFD_TRY(launch_prepare_values(H, P.alpha, P.beta, P.chunk_rid, P.rcoef, P.rcoef_ld, ws.prep, ws.prep_bytes,
                                       stream));
@@ -343,12 +349,25 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
             A.vin = va; A.ldin = n_b; A.w = vb; A.ldw = n_b; A.x = xb; A.ldx = ldx;
             A.a = 2.0 * P.alpha; A.p = 2; A.dots = moments ? ws.raw + 2 * n_b : nullptr;
             CFD_TRY(launch_step<T>(STEP_SECOND, n_b, vpt, A, P.grid_cap, stream));
+            if (dw && n_p >= 3) {
+                // the recurrence blocks and X_b to double-word form; the last
+                // general step writes X_b back as complex double
+                CFD_TRY(launch_dw_convert(va, n_b, X.n_rows, n_b, true, stream));
+                CFD_TRY(launch_dw_convert(vb, n_b, X.n_rows, n_b, true, stream));
+                CFD_TRY(launch_dw_convert(xb, ldx, X.n_rows, n_b, true, stream));
+            }
             // steps 3..n_p: swap(V_prev, V_cur); V_prev = 2 H~ V_cur - V_prev; X_b += gc_p V_prev
             for (int p = 3; p <= n_p; ++p) {
                 C *cur = (p & 1) ? vb : va;
                 C *prev = (p & 1) ? va : vb;
                 A.vin = cur; A.ldin = n_b; A.w = prev; A.ldw = n_b; A.p = p;
                 A.dots = moments ? ws.raw + (int64_t)(p - 1) * 2 * n_b : nullptr;
+                if constexpr (std::is_same<T, double>::value) {
+                    if (dw) {
+                        CFD_TRY(launch_step_dw(n_b, vpt, A, p == n_p, P.grid_cap, stream));
+                        continue;
+                    }
+                }
                 CFD_TRY(launch_step<T>(STEP_GENERAL, n_b, vpt, A, P.grid_cap, stream));
             }
             if (moments)
@@ -362,7 +381,7 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
     return CFD_OK;
 }
 
-static cfd_status check_filter_args(const cfd_matrix *H, int n_p, const cfd_block &X, int n_b, int vpt) {
+cfd_status check_filter_args(const cfd_matrix *H, int n_p, const cfd_block &X, int n_b, int vpt) {
     CFD_TRY(check_matrix(H));
     CFD_TRY(validate_block(X, H->n_rows));
     if (n_p < 2) return fail(CFD_ERR_ARG, "n_p=%d < 2", n_p);
@@ -396,8 +415,16 @@ static FilterScratch carve_filter(const cfd_matrix *H, const cfd_block &X, int n
 cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
                             const cfd_block &X, int n_b, int vpt, int grid_cap, int persistent, int staged,
                             void *work, size_t work_bytes, double *moments, cudaStream_t stream, int gather,
-                            int fixed_chunk) {
+                            int fixed_chunk, int arith) {
     CFD_TRY(check_filter_args(H, n_p, X, n_b, vpt));
+    if (arith != ARITH_NATIVE && arith != ARITH_DW) return fail(CFD_ERR_ARG, "arith=%d not in {0, 1}", arith);
+    if (arith == ARITH_DW) {
+        if (H->prec != CFD_C128 || X.prec != CFD_C128)
+            return fail(CFD_ERR_ARG, "double-word arithmetic is for complex-double matrices and blocks");
+        if (!(H->flags & CFD_MATRIX_PACKED))
+            return fail(CFD_ERR_ARG, "double-word arithmetic needs packed matrix values (CFD_PACK_RI)");
+        if (persistent) return fail(CFD_ERR_ARG, "the persistent filter has no double-word variant");
+    }
     if (!(lmin < lmax) || !(lmin <= lam_l && lam_l < lam_r && lam_r <= lmax))
         return fail(CFD_ERR_ARG, "need lmin <= lam_l < lam_r <= lmax (got %g %g %g %g)", lmin, lam_l, lam_r, lmax);
     if (persistent && moments) return fail(CFD_ERR_ARG, "the persistent filter records no moments");
@@ -417,6 +444,7 @@ cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, doubl
     P.staged = staged > 0 ? staged : (staged < 0 ? 0 : (int)default_staged(H->prec));
     P.gather = gather > 0 ? gather : default_gather(H->prec);
     P.fixed_chunk = fixed_chunk;
+    P.arith = arith;
     P.alpha = 2.0 / (lmax - lmin);
     P.beta = 0.5 * (lmax + lmin);
     CFD_TRY(launch_filter_coeffs(P.alpha, P.beta, lam_l, lam_r, n_p, ws.gc, stream));
@@ -574,12 +602,13 @@ cfd_status cfd_filter_ex(const cfd_matrix *H, double lmin, double lmax, double l
     int staged = opts ? opts->staged : 0;
     int gather = opts ? opts->gather : 0;
     int fixed_chunk = opts ? opts->fixed_chunk : 0;
+    int arith = opts ? opts->arith : 0;
     if (cap < 0) return fail(CFD_ERR_ARG, "grid_cap < 0");
     if (staged < -1 || staged > 2) return fail(CFD_ERR_ARG, "staged=%d not in -1..2", staged);
     if (gather != 0 && gather != 4 && gather != 8 && gather != STEP_GATHER_ALL)
         return fail(CFD_ERR_ARG, "gather=%d not in {0, 4, 8, %d}", gather, STEP_GATHER_ALL);
     return filter_impl_opts(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, vpt, cap, pers, staged, work, work_bytes,
-                            moments, stream, gather, fixed_chunk);
+                            moments, stream, gather, fixed_chunk, arith);
 }
 
 cfd_status cfd_kpm_moments(const cfd_matrix *H, double lmin, double lmax, int n_p, cfd_block R, int n_b, void *work,
@@ -595,6 +624,10 @@ cfd_status cfd_workspace_status(const void *work, cudaStream_t stream) {
     CFD_CUDA(cudaMemcpyAsync(&st, work, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CFD_CUDA(cudaStreamSynchronize(stream));
     if (st == CFD_ERR_TIMEOUT) return fail(CFD_ERR_TIMEOUT, "a bounded device-side wait expired");
+    if (st == (CFD_ERR_TIMEOUT | CFD_STATUS_DRAIN_EXPIRED))
+        return fail(CFD_ERR_TIMEOUT,
+                    "a bounded device-side wait expired and copies of that launch may still have been in flight "
+                    "when it returned: the results and the contents of this workspace are invalid");
     if (st == CFD_ERR_BOUNDS)
         return fail(CFD_ERR_BOUNDS, "a Chebyshev moment exceeded mu_0: [lmin, lmax] does not contain the spectrum");
     if (st != 0) return fail(CFD_ERR_INTERNAL, "device status %d", st);

@@ -74,6 +74,19 @@ template <typename T>
 cfd_status launch_persistent(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> *xb,
                              int64_t ldx, int n_p, int grid_cap, cudaStream_t stream);
 
+// Complex-double general steps in double-word arithmetic on the fp32 pipe
+// (step_dw.cu): the step for general step p (last: X written back as
+// complex double), the in-place conversion of a block between complex double
+// and double-word form, and the double-word prepared values.
+cfd_status launch_step_dw(int nb, int vpt, const StepArgs<double> &A, bool last, int grid_cap, cudaStream_t s);
+cfd_status launch_dw_convert(void *p, int64_t ld, int64_t n_rows, int nb, bool to_dw, cudaStream_t stream);
+cfd_status launch_prepare_values_dw(const cfd_matrix *H, double alpha, double beta, const int32_t *chunk_rid,
+                                    const double *rcoef, int64_t rcoef_ld, void *out, size_t out_bytes,
+                                    cudaStream_t stream);
+
+// Arithmetic of the complex-double filter's general steps.
+enum FilterArith : int { ARITH_NATIVE = 0, ARITH_DW = 1 };
+
 // How one filter application is run.
 struct FilterPlan {
     int n_b = 0, n_p = 0, vpt = 0, grid_cap = 0;
@@ -81,6 +94,7 @@ struct FilterPlan {
     int staged = 0;
     int gather = 0;
     int fixed_chunk = 0;
+    int arith = ARITH_NATIVE;
     double alpha = 0, beta = 0;
     const int32_t *chunk_rid = nullptr;   // batch: chunk -> realisation
     const double *rcoef = nullptr;        // batch: per realisation {alpha, beta, weights}
@@ -108,6 +122,12 @@ int default_gather(int prec);
 int default_vpt(int prec, int n_b);
 size_t filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int prec_X);
 cfd_status validate_block(const cfd_block &X, int64_t n_rows);
+// Matrix, block, degree, block width, precision pair and vectors per thread
+// of a filter call (CFD_ERR_ARG with a message on the first violation).
+cfd_status check_filter_args(const cfd_matrix *H, int n_p, const cfd_block &X, int n_b, int vpt);
+// Bit or-ed into CFD_ERR_TIMEOUT in a workspace status word when a CTA also
+// gave up waiting for its own bulk copies to land before it returned.
+constexpr int CFD_STATUS_DRAIN_EXPIRED = 0x100;
 cfd_status launch_filter_coeffs(double alpha, double beta, double lam_l, double lam_r, int n_p,
                                 double *gc, cudaStream_t stream);
 // Values of 2 alpha (H - beta) in H's SELL layout and storage into out
@@ -129,7 +149,7 @@ cfd_status launch_widen(const float2 *src, int64_t lds, double2 *dst, int64_t ld
 cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
                             const cfd_block &X, int n_b, int vpt, int grid_cap, int persistent, int staged,
                             void *work, size_t work_bytes, double *moments, cudaStream_t stream, int gather = 0,
-                            int fixed_chunk = 0);
+                            int fixed_chunk = 0, int arith = ARITH_NATIVE);
 size_t batched_workspace(int64_t N, int R, int n_s, int n_b, int n_p, int prec_H, int prec_X);
 cfd_status kpm_impl(const cfd_matrix *H, double lmin, double lmax, int n_p, const cfd_block &R, int n_b,
                     void *work, size_t work_bytes, double *moments, cudaStream_t stream);

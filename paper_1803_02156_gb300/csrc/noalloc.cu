@@ -7,8 +7,6 @@
 // cudaMalloc's cost and its implicit device-wide synchronisation.  Such
 // callers pass only their inputs and outputs; the work blocks, weights,
 // per-step dot products and reduction partials live in cfd_noalloc_scratch.
-#include <mutex>
-
 #include "filter.cuh"
 
 namespace cfd {
@@ -17,27 +15,22 @@ namespace {
 // One copy per device that loads the library, held until process exit.
 static __device__ __align__(256) unsigned char cfd_noalloc_scratch[CFD_NOALLOC_SCRATCH_BYTES];
 
-// Device address of the scratch array, looked up once per device with that
-// device current.  In host code the symbol is only a host-side handle, so the
-// kernels must be given this address instead.
-constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
+// Device address of the scratch array on the current device.  In host code
+// the symbol is only a host-side handle, so the kernels must be given this
+// address instead.  Looked up on every call (no allocation, no stream work):
+// a cached address would go stale if the module were loaded again in a new
+// context (after cudaDeviceReset), and the kernels would then write through a
+// dangling pointer.  The first lookup on a device may load the module, which
+// is why the first call there must come before any stream capture.
 cfd_status scratch_for_current_device(void **out) {
     int dev = -1;
     CFD_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(CFD_ERR_ARG, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, cfd_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(CFD_ERR_CUDA, "cudaGetSymbolAddress(cfd_noalloc_scratch) failed on device %d: %s", dev,
-                        cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, cfd_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(CFD_ERR_CUDA, "cudaGetSymbolAddress(cfd_noalloc_scratch) failed on device %d: %s", dev,
+                    cudaGetErrorString(e));
+    *out = p;
     return CFD_OK;
 }
 
@@ -51,8 +44,8 @@ extern "C" {
 cfd_status cfd_filter_noalloc(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
                               cfd_block X, int n_b, double *moments, cudaStream_t stream) {
     clear_error();
-    CFD_TRY(check_matrix(H));
-    if (n_b < 1 || n_p < 2 || X.n_cols < 1) return fail(CFD_ERR_ARG, "cfd_filter_noalloc: bad sizes");
+    // the real argument errors first, then whether the problem fits
+    CFD_TRY(check_filter_args(H, n_p, X, n_b, 0));
     size_t need = filter_workspace(H->n_rows, X.n_cols, n_b, n_p, H->prec, X.prec);
     if (need > (size_t)CFD_NOALLOC_SCRATCH_BYTES)
         return fail(CFD_ERR_ARG,
@@ -63,6 +56,14 @@ cfd_status cfd_filter_noalloc(const cfd_matrix *H, double lmin, double lmax, dou
     CFD_TRY(scratch_for_current_device(&scratch));
     return filter_impl(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, 0, 0, scratch, (size_t)CFD_NOALLOC_SCRATCH_BYTES,
                        moments, stream);
+}
+
+cfd_status cfd_filter_noalloc_status(cudaStream_t stream) {
+    clear_error();
+    void *scratch = nullptr;
+    CFD_TRY(scratch_for_current_device(&scratch));
+    // the filter carves its status word from the start of the scratch
+    return cfd_workspace_status(scratch, stream);
 }
 
 }  // extern "C"

@@ -66,15 +66,19 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
     CFD_TRY(check_matrix(H));
     if (!p || !evals || !resid || !res || !work) return fail(CFD_ERR_ARG, "NULL argument");
     if (H->prec != CFD_C128) return fail(CFD_ERR_ARG, "cfd_solve needs the complex-double matrix as H");
-    const bool mixed = p->policy == CFD_POLICY_MIXED;
+    if (p->policy < CFD_POLICY_FP64 || p->policy > CFD_POLICY_MIXED_DW)
+        return fail(CFD_ERR_ARG, "unknown policy %d", p->policy);
+    const bool mixed = p->policy == CFD_POLICY_MIXED || p->policy == CFD_POLICY_MIXED_DW;
+    // complex-double filter applications in double-word arithmetic
+    const bool dw = p->policy == CFD_POLICY_FP64_DW || p->policy == CFD_POLICY_MIXED_DW;
     if (mixed) {
         if (!H_low) return fail(CFD_ERR_ARG, "mixed policy needs the complex-float matrix H_low");
         CFD_TRY(check_matrix(H_low));
         if (H_low->prec != CFD_C64 || H_low->n_rows != H->n_rows)
             return fail(CFD_ERR_ARG, "H_low must be the complex-float copy of H");
-    } else if (p->policy != CFD_POLICY_FP64) {
-        return fail(CFD_ERR_ARG, "unknown policy %d", p->policy);
     }
+    if (dw && !(H->flags & CFD_MATRIX_PACKED))
+        return fail(CFD_ERR_ARG, "double-word policies need H with packed values (CFD_PACK_RI)");
     if (X.prec != CFD_C128 || X.n_cols != p->n_s || X.n_rows != H->n_rows)
         return fail(CFD_ERR_ARG, "X must be the N x n_s complex-double block");
     if (!(p->lam_l < p->lam_r)) return fail(CFD_ERR_ARG, "empty search window");
@@ -119,8 +123,9 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
     for (int it = 1; it <= p->max_iter; ++it) {
         cudaEvent_t e0 = ev.e[0], e1 = ev.e[1], e2 = ev.e[2], e3 = ev.e[3];
         cudaEventRecord(e0, stream);
-        CFD_TRY(filter_impl(tr.low ? H_low : H, lmin, lmax, p->lam_l, p->lam_r, p->n_p, X, p->n_b, 0, 0, scratch,
-                            scratch_bytes, nullptr, stream));
+        CFD_TRY(filter_impl_opts(tr.low ? H_low : H, lmin, lmax, p->lam_l, p->lam_r, p->n_p, X, p->n_b, 0, 0, 0, 0,
+                                 scratch, scratch_bytes, nullptr, stream, 0, 0,
+                                 (dw && !tr.low) ? ARITH_DW : ARITH_NATIVE));
         cudaEventRecord(e1, stream);
         int rank = n;
         CFD_TRY(orthogonalize_impl(X, 1e-14, nullptr, reinterpret_cast<int *>(small + 8), scratch, scratch_bytes,
@@ -134,7 +139,7 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
         int dev_status = 0;          // the filter workspace starts with its status word
         CFD_CUDA(cudaMemcpyAsync(&dev_status, scratch, sizeof(int), cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaStreamSynchronize(stream));
-        if (dev_status == CFD_ERR_TIMEOUT) return fail(CFD_ERR_TIMEOUT, "a bounded device-side wait expired");
+        if ((dev_status & 0xff) == CFD_ERR_TIMEOUT) return fail(CFD_ERR_TIMEOUT, "a bounded device-side wait expired");
         const float a = ev.ms(0, 1), b = ev.ms(1, 2), c = ev.ms(2, 3);
         res->t_filter += a * 1e-3;
         res->t_orth += b * 1e-3;

@@ -1,0 +1,444 @@
+// General fused ChebFD step (Algorithm 1, lines 9-12) for complex double data
+// in double-word arithmetic on the fp32 pipe.
+//
+// GB300 executes fp64 fused multiply-adds at 1/64 of the fp32 rate, so the
+// native complex128 step is bound by the FP64 pipe at about a fifth of the
+// HBM bandwidth.  Here every double is carried as an unevaluated sum of two
+// floats hi + lo (|lo| <= ulp(hi) / 2, about 48 significant bits; Dekker
+// 1971, "A floating-point technique for extending the available precision")
+// and every operation of the step runs on the fp32 pipe:
+//   * products exactly as hi*hi plus its rounding error from one FMA
+//     (Dekker's TwoProduct via FMA) plus the two cross terms hi*lo, lo*hi;
+//   * sums with Knuth's TwoSum (exact error of a rounded addition), the
+//     error terms of a row sum collected in a second float and added once
+//     at the end (the accumulation of Ogita, Rump and Oishi 2005, "Accurate
+//     sum and dot product", Dot2);
+//   * the result renormalised with TwoSum.
+// Each operation is accurate to a few units of 2^-48 relative to the sum of
+// the magnitudes of its terms (lo*lo products, below 2^-48 |hi*hi|, are
+// dropped), against 2^-53 for native fp64.
+//
+// Storage stays 16 bytes per complex element: the recurrence blocks V_a, V_b
+// and, during one filter application, the caller's X block hold the
+// double-word form {re_hi, im_hi, re_lo, im_lo}; the driver converts X to it
+// after step 2 and back to complex double after the last step.  The matrix
+// values are prepared once per application as the double-word form of
+// 2 alpha (H - beta) (8 bytes per packed slot, the bytes of a packed double),
+// so the minimum traffic per step equals the native step's.
+#include "step_kernels.cuh"
+
+namespace cfd {
+
+namespace {
+
+// s + e = a + b exactly, s = fl(a + b) (Knuth's TwoSum; no contraction).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+// (s, e) += (ah + al) (bh + bl): the product's high part enters s through
+// TwoSum, its rounding error, the cross terms and the sum's error enter e.
+__device__ __forceinline__ void dw_mac(float &s, float &e, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float pe = __fmaf_rn(ah, bh, -p);
+    pe = __fmaf_rn(ah, bl, pe);
+    pe = __fmaf_rn(al, bh, pe);
+    float t, err;
+    two_sum(s, p, t, err);
+    s = t;
+    e = __fadd_rn(e, __fadd_rn(err, pe));
+}
+
+// x + g v for double-words x = (xh, xl), g = (gh, gl), v = (vh, vl), renormalised.
+__device__ __forceinline__ void dw_axpy(float &xh, float &xl, float gh, float gl, float vh, float vl) {
+    const float p = __fmul_rn(gh, vh);
+    float pe = __fmaf_rn(gh, vh, -p);
+    pe = __fmaf_rn(gh, vl, pe);
+    pe = __fmaf_rn(gl, vh, pe);
+    float t, err;
+    two_sum(xh, p, t, err);
+    const float lo = __fadd_rn(xl, __fadd_rn(pe, err));
+    xh = __fadd_rn(t, lo);
+    xl = __fsub_rn(lo, __fsub_rn(xh, t));
+}
+
+__device__ __forceinline__ float4 ld_nc4(const float4 *p) { return __ldg(p); }
+
+}  // namespace
+
+// Arguments: those of the native general step (StepArgs<double>); the block
+// pointers hold double-words, prep_val the double-word prepared values
+// (float2 {hi, lo} per slot).  LAST: X is written back as complex double.
+// EARLY: a row's X and own V_cur entries are loaded before its gathers (their
+// latency overlaps the row sum, registers held across it: two CTAs per SM);
+// else after the row sum (three CTAs per SM).
+template <int NB, int VPT, bool MOM, int CH, bool LAST, bool EARLY>
+__global__ void __launch_bounds__(STEP_WARPS * 32, EARLY ? 2 : 3)
+k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
+    constexpr int TPR = NB / VPT;
+    constexpr int RPW = 32 / TPR;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_len[2];
+    const int col_bytes = (int)round_up_dev((size_t)slots_cap * 4, 16);
+    auto col_s = [&](int b) { return reinterpret_cast<int32_t *>(smem_raw + b * col_bytes); };
+    auto val_s = [&](int b) {
+        return reinterpret_cast<float2 *>(smem_raw + 2 * col_bytes + (size_t)b * slots_cap * sizeof(float2));
+    };
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int sub = lane / TPR;
+    const int j0 = (lane % TPR) * VPT;
+    const int log2C = CH > 0 ? __ffs(CH) - 1 : A.H.log2C;
+    const int chunk_h = CH > 0 ? CH : 1 << log2C;
+    const int64_t n_rows = A.H.n_rows;
+    const int64_t n_chunks = (n_rows + chunk_h - 1) >> log2C;
+    const float2 *gval = reinterpret_cast<const float2 *>(A.prep_val);
+    const float4 *vin = reinterpret_cast<const float4 *>(A.vin);
+    float4 *wout = reinterpret_cast<float4 *>(A.w);
+    float4 *xdw = reinterpret_cast<float4 *>(A.x);
+    const uint32_t tx_extra = A.staged == 2 ? 16u : 0u;
+    const long long limit = A.staged == 2 ? (1LL << 24) : (1LL << 32);
+    // the step's weight g_p c_p as a double-word (in a batch: per chunk, that
+    // of the chunk's realisation)
+    float gh = 0.f, gl = 0.f;
+    auto set_weight = [&](double gd) {
+        gh = __double2float_rn(gd);
+        gl = __double2float_rn(gd - (double)gh);
+    };
+    if (!A.chunk_rid) set_weight(A.gc[A.p]);
+    // 32-bit gather offsets (16-byte units) when the chunk height is compiled in
+    const uint32_t ld16 = (uint32_t)A.ldin;
+    float uu_s[VPT], uu_e[VPT], wu_s[VPT], wu_e[VPT];
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) uu_s[q] = uu_e[q] = wu_s[q] = wu_e[q] = 0.f;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int64_t c, int b) {     // thread 0: stage chunk c into buffer b
+        const int cl = __ldg(A.H.chunk_len + c);
+        const int len = (cl & 0xffff) + (cl >> 16);
+        const int64_t base = __ldg(A.H.chunk_ptr + c);
+        const uint32_t nslot = (uint32_t)len << log2C;
+        s_len[b] = cl;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[b], nslot * (uint32_t)(4 + sizeof(float2)) + tx_extra);
+        if (nslot) {
+            tma_load_1d(col_s(b), A.H.col + base, nslot * 4u, &bar[b]);
+            tma_load_1d(val_s(b), gval + base, nslot * (uint32_t)sizeof(float2), &bar[b]);
+        }
+    };
+
+    int k = 0;
+    bool ok = true;
+    bool prefetched = false;
+    if (tid == 0 && (int64_t)blockIdx.x < n_chunks) issue(blockIdx.x, 0);
+    __syncthreads();
+    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++k) {
+        const int b = k & 1;
+        prefetched = c + gridDim.x < n_chunks;
+        if (tid == 0 && prefetched) issue(c + gridDim.x, b ^ 1);
+        const bool landed = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);
+        if (landed) {
+            const int cl = s_len[b];
+            const int nre = cl & 0xffff;
+            const int len = nre + (cl >> 16);
+            if (A.chunk_rid) set_weight(__ldg(A.rcoef + (int64_t)__ldg(A.chunk_rid + c) * A.rcoef_ld + 2 + A.p));
+            for (int rr = warp * RPW + sub; rr < chunk_h; rr += STEP_WARPS * RPW) {
+                const int64_t r = (c << log2C) + rr;
+                if (r >= n_rows) continue;
+                const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
+                const int32_t *colp = col_s(b) + rr;
+                const float2 *valp = val_s(b) + rr;
+                // V_prev starts the row sum; the own row of V_cur (moments)
+                // and X are loaded here or after the sum (EARLY)
+                float4 u[VPT], wo[VPT], xo[VPT];
+                auto load_epilogue = [&]() {
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) {
+                        if (MOM) u[q] = ld_nc4(vin + i * A.ldin + j0 + q);
+                        xo[q] = xdw[i * A.ldx + j0 + q];
+                    }
+                };
+#pragma unroll
+                for (int q = 0; q < VPT; ++q) wo[q] = wout[i * A.ldw + j0 + q];
+                if (EARLY) load_epilogue();
+                // row sum started at -V_prev: (s, e) per real and imaginary part
+                float rs[VPT], re[VPT], is[VPT], ie[VPT];
+#pragma unroll
+                for (int q = 0; q < VPT; ++q) {
+                    rs[q] = -wo[q].x; re[q] = -wo[q].z;
+                    is[q] = -wo[q].y; ie[q] = -wo[q].w;
+                }
+                auto gather = [&](int kk, float4 (&v)[VPT]) {
+                    const int cc = max(colp[kk << log2C], 0);          // padding: col -1, value 0
+                    if constexpr (CH > 0) {
+                        const float4 *row = vin + (uint64_t)((uint32_t)cc * ld16) + j0;
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q) v[q] = ld_nc4(row + q);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q) v[q] = ld_nc4(vin + (int64_t)cc * A.ldin + j0 + q);
+                    }
+                };
+                auto madd = [&](int kk, bool imag, const float4 (&v)[VPT]) {
+                    const float2 h = valp[kk << log2C];
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) {
+                        if (imag) {            // i h v: (-h v_im, h v_re)
+                            dw_mac(rs[q], re[q], -h.x, -h.y, v[q].y, v[q].w);
+                            dw_mac(is[q], ie[q], h.x, h.y, v[q].x, v[q].z);
+                        } else {
+                            dw_mac(rs[q], re[q], h.x, h.y, v[q].x, v[q].z);
+                            dw_mac(is[q], ie[q], h.x, h.y, v[q].y, v[q].w);
+                        }
+                    }
+                };
+                constexpr int U = 4;
+                for (int g = 0; g < 2; ++g) {             // real group, then imaginary group
+                    const bool imag = g == 1;
+                    int kk = imag ? nre : 0;
+                    const int k1 = imag ? len : nre;
+                    for (; kk + U <= k1; kk += U) {
+                        float4 vv[U][VPT];
+#pragma unroll
+                        for (int uo = 0; uo < U; ++uo) gather(kk + uo, vv[uo]);
+#pragma unroll
+                        for (int uo = 0; uo < U; ++uo) madd(kk + uo, imag, vv[uo]);
+                    }
+                    for (; kk < k1; ++kk) {
+                        float4 v[VPT];
+                        gather(kk, v);
+                        madd(kk, imag, v);
+                    }
+                }
+                if (!EARLY) load_epilogue();
+                // V_new = the renormalised sum; X += g V_new; moments
+#pragma unroll
+                for (int q = 0; q < VPT; ++q) {
+                    float4 wn;
+                    two_sum(rs[q], re[q], wn.x, wn.z);
+                    two_sum(is[q], ie[q], wn.y, wn.w);
+                    wout[i * A.ldw + j0 + q] = wn;
+                    float xrh = xo[q].x, xrl = xo[q].z, xih = xo[q].y, xil = xo[q].w;
+                    dw_axpy(xrh, xrl, gh, gl, wn.x, wn.z);
+                    dw_axpy(xih, xil, gh, gl, wn.y, wn.w);
+                    if (LAST) {
+                        double2 *xd = reinterpret_cast<double2 *>(xdw + i * A.ldx + j0 + q);
+                        *xd = make_double2((double)xrh + (double)xrl, (double)xih + (double)xil);
+                    } else {
+                        xdw[i * A.ldx + j0 + q] = make_float4(xrh, xih, xrl, xil);
+                    }
+                    if (MOM) {
+                        dw_mac(uu_s[q], uu_e[q], u[q].x, u[q].z, u[q].x, u[q].z);
+                        dw_mac(uu_s[q], uu_e[q], u[q].y, u[q].w, u[q].y, u[q].w);
+                        dw_mac(wu_s[q], wu_e[q], wn.x, wn.z, u[q].x, u[q].z);
+                        dw_mac(wu_s[q], wu_e[q], wn.y, wn.w, u[q].y, u[q].w);
+                    }
+                }
+            }
+        }
+        if (!__syncthreads_and(landed)) {
+            ok = false;
+            break;
+        }
+    }
+    if (!ok) {
+        if (tid == 0) {
+            const int b = k & 1;
+            if (tx_extra) {
+                mbar_complete_tx(&bar[b], tx_extra);
+                if (prefetched) mbar_complete_tx(&bar[b ^ 1], tx_extra);
+            }
+            const long long drain_limit = 1LL << 32;
+            bool drained = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), drain_limit);
+            if (prefetched)
+                drained = mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1), drain_limit) && drained;
+            atomicOr(A.status, drained ? (int)CFD_ERR_TIMEOUT : (int)CFD_ERR_TIMEOUT | CFD_STATUS_DRAIN_EXPIRED);
+        }
+        return;
+    }
+    if (MOM) {
+        // the threads' double-word sums (s + e) as Kahan-form accumulators
+        // (value s - c) for the shared deterministic reduction
+        MomentAcc<float> uu[VPT], wu[VPT];
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            uu[q].s = uu_s[q]; uu[q].c = -uu_e[q];
+            wu[q].s = wu_s[q]; wu[q].c = -wu_e[q];
+        }
+        reduce_moments<float, NB, VPT>(A.partial, A.ticket, A.dots, uu, wu);
+    }
+}
+
+// ------------------------------------------------------------ conversions --
+
+// In place, N x nb complex elements of a block with row stride ld (elements):
+// complex double -> double-word {re_hi, im_hi, re_lo, im_lo} (TO_DW) or back.
+// hi = fl32(x), lo = fl32(x - hi): x - hi is exact in fp64, so hi + lo is x
+// rounded to 48 bits; back: hi + lo evaluated in fp64 (exact).
+template <bool TO_DW>
+__global__ void k_dw_convert(double2 *p, int64_t ld, int64_t n_rows, int nb) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n_rows * nb) return;
+    const int64_t i = e / nb;
+    const int j = (int)(e % nb);
+    double2 *a = p + i * ld + j;
+    if (TO_DW) {
+        const double2 z = *a;
+        const float rh = __double2float_rn(z.x), ih = __double2float_rn(z.y);
+        const float rl = __double2float_rn(z.x - (double)rh), il = __double2float_rn(z.y - (double)ih);
+        *reinterpret_cast<float4 *>(a) = make_float4(rh, ih, rl, il);
+    } else {
+        const float4 d = *reinterpret_cast<const float4 *>(a);
+        *a = make_double2((double)d.x + (double)d.z, (double)d.y + (double)d.w);
+    }
+}
+
+// Prepared values 2 alpha (H - beta) as double-words {hi, lo}, one per packed
+// slot, in H's SELL layout (the double-word form of k_prepare_values' output).
+__global__ void k_prepare_values_dw(SellView<double> H, int64_t n_pos, double alpha, double beta,
+                                    const int32_t *chunk_rid, const double *rcoef, int64_t rcoef_ld, float2 *out) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_pos) return;
+    const int64_t ch = r >> H.log2C;
+    const int64_t base = H.chunk_ptr[ch] + (r & ((1 << H.log2C) - 1));
+    const int cl = H.chunk_len[ch];
+    const int len = (cl & 0xffff) + (cl >> 16);
+    const int64_t i = r < H.n_rows ? (H.perm ? (int64_t)H.perm[r] : r) : -2;
+    if (chunk_rid) {
+        const double *rc = rcoef + (int64_t)chunk_rid[ch] * rcoef_ld;
+        alpha = rc[0];
+        beta = rc[1];
+    }
+    const double a2 = 2.0 * alpha;
+    for (int k = 0; k < len; ++k) {
+        const int64_t s = base + ((int64_t)k << H.log2C);
+        const double h = H.pval[s];
+        const double v = H.col[s] == i ? a2 * (h - beta) : a2 * h;
+        const float hi = __double2float_rn(v);
+        out[s] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+
+// ---------------------------------------------------------------- launch --
+
+namespace {
+
+template <int NB, int VPT, bool MOM, int CH, bool LAST, bool EARLY>
+cfd_status launch_dw_t(const StepArgs<double> &A, int grid_cap, cudaStream_t stream) {
+    const int slots_cap = A.H.slots_bound << A.H.log2C;
+    if (slots_cap <= 0) return fail(CFD_ERR_ARG, "matrix has no slot bound; cannot stage");
+    const size_t smem = 2 * round_up((size_t)slots_cap * 4, 16) + round_up(2 * (size_t)slots_cap * sizeof(float2), 16);
+    if (smem > 200 * 1024) return fail(CFD_ERR_ARG, "chunk too large to stage (%zu bytes)", smem);
+    auto kern = k_cheb_step_dw<NB, VPT, MOM, CH, LAST, EARLY>;
+    struct Cache {
+        std::mutex mu;
+        int occ[64];
+        size_t occ_smem[64];
+        size_t attr_smem[64];
+    };
+    static Cache cache{};
+    int dev = 0;
+    CFD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CFD_ERR_ARG, "device ordinal %d out of range", dev);
+    int resident = 0;
+    {
+        std::lock_guard<std::mutex> lock(cache.mu);
+        if (smem > cache.attr_smem[dev]) {
+            CFD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            cache.attr_smem[dev] = smem;
+        }
+        if (cache.occ[dev] == 0 || cache.occ_smem[dev] != smem) {
+            int o = 0;
+            CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, STEP_WARPS * 32, smem));
+            cache.occ[dev] = std::max(1, std::min(o, STEP_MAX_CTAS_PER_SM));
+            cache.occ_smem[dev] = smem;
+        }
+        resident = cache.occ[dev];
+    }
+    const int64_t n_chunks = (A.H.n_rows + (1LL << A.H.log2C) - 1) >> A.H.log2C;
+    int64_t grid = std::min<int64_t>((int64_t)resident * sm_count(), n_chunks);
+    if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
+    grid = std::max<int64_t>(grid, 1);
+    kern<<<(unsigned)grid, STEP_WARPS * 32, smem, stream>>>(A, slots_cap);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    return CFD_OK;
+}
+
+template <int NB, int VPT, bool MOM>
+cfd_status launch_dw_m(const StepArgs<double> &A, bool last, bool early, int grid_cap, cudaStream_t s) {
+    // chunk height 32 compiled in when the gathers' 16-byte offsets fit in 32 bits
+    const bool fixed = A.H.log2C == 5 && (uint64_t)A.H.n_rows * (uint64_t)A.ldin < (1ULL << 32);
+#define CFD_DW_L(CH_)                                                                            \
+    if (early) return last ? launch_dw_t<NB, VPT, MOM, CH_, true, true>(A, grid_cap, s)           \
+                           : launch_dw_t<NB, VPT, MOM, CH_, false, true>(A, grid_cap, s);          \
+    return last ? launch_dw_t<NB, VPT, MOM, CH_, true, false>(A, grid_cap, s)                     \
+                : launch_dw_t<NB, VPT, MOM, CH_, false, false>(A, grid_cap, s);
+    if (fixed) {
+        CFD_DW_L(32)
+    }
+    CFD_DW_L(0)
+#undef CFD_DW_L
+}
+
+}  // namespace
+
+// vpt: the native step's default for complex double (1 at n_b = 8, else 2)
+// or that value given explicitly.  early: the epilogue loads before the
+// gathers (the gather = 16 option), else after the row sum.
+cfd_status launch_step_dw(int nb, int vpt, const StepArgs<double> &A, bool last, int grid_cap, cudaStream_t s) {
+    if (!A.H.packed) return fail(CFD_ERR_ARG, "double-word arithmetic needs packed matrix values (CFD_PACK_RI)");
+    if (!A.status || !A.prep_val) return fail(CFD_ERR_INTERNAL, "double-word step without status or prepared values");
+    const bool mom = A.dots != nullptr;
+    const bool early = A.gather >= STEP_GATHER_ALL;
+#define CFD_DW_CASE(NB_, VPT_)                                                                   \
+    if (nb == NB_ && vpt == VPT_)                                                                \
+        return mom ? launch_dw_m<NB_, VPT_, true>(A, last, early, grid_cap, s)                   \
+                   : launch_dw_m<NB_, VPT_, false>(A, last, early, grid_cap, s);
+    CFD_DW_CASE(8, 1)
+    CFD_DW_CASE(16, 2)
+    CFD_DW_CASE(32, 2)
+    CFD_DW_CASE(64, 2)
+#undef CFD_DW_CASE
+    return fail(CFD_ERR_ARG, "double-word step: n_b=%d with %d vectors per thread is not built (vpt 1 at n_b = 8, "
+                "else 2)", nb, vpt);
+}
+
+cfd_status launch_dw_convert(void *p, int64_t ld, int64_t n_rows, int nb, bool to_dw, cudaStream_t stream) {
+    const int64_t n = n_rows * nb;
+    if (n == 0) return CFD_OK;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (to_dw) k_dw_convert<true><<<grid, 256, 0, stream>>>(static_cast<double2 *>(p), ld, n_rows, nb);
+    else k_dw_convert<false><<<grid, 256, 0, stream>>>(static_cast<double2 *>(p), ld, n_rows, nb);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    return CFD_OK;
+}
+
+cfd_status launch_prepare_values_dw(const cfd_matrix *H, double alpha, double beta, const int32_t *chunk_rid,
+                                    const double *rcoef, int64_t rcoef_ld, void *out, size_t out_bytes,
+                                    cudaStream_t stream) {
+    const SellView<double> v = sell_view<double>(H);
+    if (!v.packed) return fail(CFD_ERR_ARG, "double-word arithmetic needs packed matrix values (CFD_PACK_RI)");
+    if ((size_t)H->n_slots * sizeof(float2) > out_bytes)
+        return fail(CFD_ERR_ARG, "matrix stores %lld slots, more than the filter workspace prepares (%d per row)",
+                    (long long)H->n_slots, kMaxRowSlots);
+    const int64_t n_pos = H->n_chunks << v.log2C;
+    if (n_pos == 0) return CFD_OK;
+    k_prepare_values_dw<<<(unsigned)((n_pos + 255) / 256), 256, 0, stream>>>(v, n_pos, alpha, beta, chunk_rid, rcoef,
+                                                                            rcoef_ld, static_cast<float2 *>(out));
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    return CFD_OK;
+}
+
+}  // namespace cfd

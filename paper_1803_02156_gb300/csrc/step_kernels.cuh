@@ -513,8 +513,8 @@ template <> struct MomentRed<float> {
 // CTA (shared memory, fixed order), then across CTAs by the last CTA to finish
 // (ticket counter), each in a fixed order.
 template <typename T, int NB, int VPT>
-__device__ __forceinline__ void reduce_moments(const StepArgs<T> &A, MomentAcc<T> (&uu)[VPT],
-                                               MomentAcc<T> (&wu)[VPT]) {
+__device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket, double *dots,
+                                               MomentAcc<T> (&uu)[VPT], MomentAcc<T> (&wu)[VPT]) {
     using Op = MomentRed<T>;
     using R = typename Op::R;
     constexpr int TPR = NB / VPT;
@@ -547,22 +547,22 @@ __device__ __forceinline__ void reduce_moments(const StepArgs<T> &A, MomentAcc<T
         R s = Op::zero();
 #pragma unroll
         for (int w = 0; w < STEP_WARPS; ++w) s = Op::add(s, red[w][e >> 1][e & 1]);
-        Op::store(A.partial + (int64_t)blockIdx.x * 2 * NB + e, s);
+        Op::store(partial + (int64_t)blockIdx.x * 2 * NB + e, s);
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last_cta = (atomicAdd(A.ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) last_cta = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     __syncthreads();
     if (last_cta) {
         __threadfence();
         for (int e = warp; e < 2 * NB; e += STEP_WARPS) {
             R s = Op::zero();
-            for (int b = lane; b < (int)gridDim.x; b += 32) s = Op::add(s, Op::load(A.partial + (int64_t)b * 2 * NB + e));
+            for (int b = lane; b < (int)gridDim.x; b += 32) s = Op::add(s, Op::load(partial + (int64_t)b * 2 * NB + e));
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) s = Op::add(s, Op::shfl_xor(s, off));
-            if (lane == 0) A.dots[e] = Op::widen(s);
+            if (lane == 0) dots[e] = Op::widen(s);
         }
-        if (threadIdx.x == 0) *A.ticket = 0u;
+        if (threadIdx.x == 0) *ticket = 0u;
     }
 }
 
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(STEP_WARPS * 32)
 k_cheb_step(const StepArgs<T> A) {
     MomentAcc<T> uu[VPT], wu[VPT];
     step_rows<T, NB, VPT, KIND, MOM, PACK>(A, uu, wu);
-    if (MOM) reduce_moments<T, NB, VPT>(A, uu, wu);
+    if (MOM) reduce_moments<T, NB, VPT>(A.partial, A.ticket, A.dots, uu, wu);
 }
 
 // ------------------------------------------------- TMA-staged general step --
@@ -608,6 +608,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// Count `bytes` of a barrier's expected transaction bytes as arrived without a
+// copy (used only to cancel the surplus the wait test expects).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
 // 1-D bulk copy global -> shared memory (TMA), completing on `bar`.
 // Addresses 16-byte aligned, size a multiple of 16 bytes.
 __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -625,10 +631,14 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
 // the new vector when it ends.  Slot counts of a chunk are
 // multiples of C >= 4, so every copy is 16-byte aligned and sized.  A wait
 // that expires (after ~2^32 cycles, about two seconds) records
-// CFD_ERR_TIMEOUT in *A.status and the CTA returns after draining its own
-// copies (bounded too).  A.staged == 2 is the test of that path: every
-// barrier expects 16 bytes more than are copied, so no wait can succeed, and
-// waits give up after 2^24 cycles.
+// CFD_ERR_TIMEOUT in *A.status and the CTA returns once its own copies in
+// flight (the current chunk's and the prefetched one's) have landed; if that
+// drain wait expires too (bounded the same way), the status also carries
+// CFD_STATUS_DRAIN_EXPIRED and the launch's results and workspace are
+// invalid.  A.staged == 2 is the test of that path: every barrier expects
+// 16 bytes more than are copied, so no chunk wait can succeed and waits give
+// up after 2^24 cycles; the drain then cancels the surplus
+// (mbarrier.complete_tx) and waits for the real copies only.
 // KMAX > 0: every gather of a row's first KMAX slots in flight at once
 // (packed values; registers capped so that two CTAs fit on an SM, three for
 // KMAX <= 8).  CH > 0:
@@ -689,11 +699,13 @@ k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
 
     int k = 0;
     bool ok = true;
+    bool prefetched = false;      // thread 0: the next chunk's copies were issued this iteration
     if (tid == 0 && (int64_t)blockIdx.x < n_chunks) issue(blockIdx.x, 0);
     __syncthreads();              // s_len[0] written by thread 0
     for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++k) {
         const int b = k & 1;
-        if (tid == 0 && c + gridDim.x < n_chunks) issue(c + gridDim.x, b ^ 1);
+        prefetched = c + gridDim.x < n_chunks;
+        if (tid == 0 && prefetched) issue(c + gridDim.x, b ^ 1);
         // every thread waits for the chunk's copies itself; a thread whose
         // wait expired skips the chunk, and the barrier below then stops all
         const bool landed = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);
@@ -719,16 +731,22 @@ k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
     }
     if (!ok) {
         if (tid == 0) {
-            atomicExch(A.status, (int)CFD_ERR_TIMEOUT);
             // drain this CTA's copies still in flight (bounded): the current
-            // chunk's and the prefetched one
+            // chunk's and, if issued, the prefetched one; in the wait test
+            // first cancel the surplus each armed barrier expects
             const int b = k & 1;
-            mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);
-            mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1), limit);
+            if (tx_extra) {
+                mbar_complete_tx(&bar[b], tx_extra);
+                if (prefetched) mbar_complete_tx(&bar[b ^ 1], tx_extra);
+            }
+            const long long drain_limit = 1LL << 32;
+            bool drained = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), drain_limit);
+            if (prefetched) drained = mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1), drain_limit) && drained;
+            atomicOr(A.status, drained ? (int)CFD_ERR_TIMEOUT : (int)CFD_ERR_TIMEOUT | CFD_STATUS_DRAIN_EXPIRED);
         }
         return;
     }
-    if (MOM) reduce_moments<T, NB, VPT>(A, uu, wu);
+    if (MOM) reduce_moments<T, NB, VPT>(A.partial, A.ticket, A.dots, uu, wu);
 }
 
 // All n_p steps of Algorithm 1 for one block in a single cooperative launch:

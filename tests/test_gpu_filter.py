@@ -155,6 +155,35 @@ def test_filter_parity_full_size_few_steps(b):
     _compare_filter(b, w.lattice, 32, 32, 6, (-0.3, 0.3))
 
 
+# fp32 bound for the 12-step full-size run below (same derivation as TOL_C64_200)
+TOL_C64_12 = 12 * 13 * 2.0 ** -24
+
+
+@pytest.mark.parametrize("prec,tol", [("c128p", TOL_C128), ("c64p", TOL_C64_12)])
+def test_bench_kernel_full_size_parity(b, prec, tol):
+    """The benchmark's kernel variant at full size: the 64x64x32 lattice
+    (N = 524288), packed real-or-imaginary values prepared as 2 alpha (H - beta),
+    TMA-staged general steps with moments, SELL C = 32, n_b = 32, for 12 steps
+    (10 general steps), against the oracle's filtered block and moments.
+    complex64: the fp32 filter on a complex128 block, as the mixed policy runs it."""
+    import torch
+    w = workloads.MEDIUM
+    n_s, n_b, n_p, win = 32, 32, 12, (-0.3, 0.3)
+    H = b.cfd_build_matrix(b.topi_params(*w.lattice, seed=w.seed), 32, 1, prec)
+    assert H.packed
+    ref = oracle.topi_csr(*w.lattice, seed=w.seed)
+    X = inputs.gaussian_block(ref.N, n_s, seed=2)
+    Xg = _gpu_block(X, torch.complex128)
+    mu = b.cfd_filter(H, -8.6, 8.6, win[0], win[1], n_p, Xg, n_b, moments=True)
+    torch.cuda.synchronize()
+    Y, dots = oracle.chebfd_filter(ref, -8.6, 8.6, win[0], win[1], n_p, X, n_b)
+    err = np.linalg.norm(Xg.cpu().numpy() - Y) / np.linalg.norm(Y)
+    muref = oracle.kpm_moments(dots)
+    merr = np.max(np.abs(mu.cpu().numpy() - muref)) / np.max(np.abs(muref))
+    assert err < tol, err
+    assert merr < tol, merr
+
+
 def test_filter_full_size_properties(b):
     """Full degree n_p = 1000 on 64x64x32: properties that hold at any size.
     mu_0 = ||x||^2 and |mu_m| <= mu_0 (|T_m| <= 1 on the scaled spectrum);

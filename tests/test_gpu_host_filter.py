@@ -39,6 +39,26 @@ def test_host_filter_equals_device_filter(b, L, n_s, n_b, n_p, prec, pinned):
     assert not np.array_equal(Xh.numpy(), X.numpy())
 
 
+@pytest.mark.parametrize("prec,tol", [("c128p", 1e-11), ("c64p", 60 * 13 * 2.0 ** -24)])
+def test_host_filter_vs_oracle(b, prec, tol):
+    """The host-memory filter against the oracle directly (block and moments):
+    8x8x8, n_s = 64 in two blocks of 32, n_p = 60."""
+    import torch
+    import oracle
+    L, n_s, n_b, n_p, win = (8, 8, 8), 64, 32, 60, (-0.7, 0.7)
+    H = b.cfd_build_matrix(b.topi_params(*L, seed=1), 32, 1, prec)
+    ref = oracle.topi_csr(*L, seed=1)
+    X = inputs.gaussian_block(ref.N, n_s, seed=2)
+    Xh = torch.from_numpy(X.copy()).pin_memory()
+    mu = b.cfd_filter_host(H, -8.6, 8.6, win[0], win[1], n_p, Xh, n_b, moments=True)
+    Y, dots = oracle.chebfd_filter(ref, -8.6, 8.6, win[0], win[1], n_p, X, n_b)
+    err = np.linalg.norm(Xh.numpy() - Y) / np.linalg.norm(Y)
+    muref = oracle.kpm_moments(dots)
+    merr = np.max(np.abs(mu.cpu().numpy() - muref)) / np.max(np.abs(muref))
+    assert err < tol, err
+    assert merr < tol, merr
+
+
 def test_host_filter_strided_host_block(b):
     """A column window of a wider host array (ld > n_s) is filtered in place;
     the other columns are untouched."""

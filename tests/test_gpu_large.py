@@ -85,11 +85,16 @@ def test_large_instance_sampled_rows(b, csr, prec, n_s, col0, tol):
     idx = torch.tensor(need, device="cuda")
     Xin = X[idx, col0:col0 + 32].cpu().numpy().astype(np.complex128)
     X_rows = {i: Xin[k] for k, i in enumerate(need)}
-    b.cfd_filter(H, -8.6, 8.6, -0.5, 0.5, N_P, X, 32)
+    n0 = (torch.linalg.norm(X[:, col0:col0 + 32].to(torch.complex128), dim=0) ** 2).cpu().numpy()
+    mu = b.cfd_filter(H, -8.6, 8.6, -0.5, 0.5, N_P, X, 32, moments=True)[col0:col0 + 32].cpu().numpy()
     got = X[torch.tensor(rows, device="cuda"), col0:col0 + 32].cpu().numpy().astype(np.complex128)
     ref = _sampled_filter(csr, X_rows, rows, -8.6, 8.6, -0.5, 0.5)
     for k, i in enumerate(rows):
         err = np.linalg.norm(got[k] - ref[i]) / max(np.linalg.norm(ref[i]), 1e-30)
         assert err < tol, (i, err)
+    # moments of the filtered block, properties that hold at any size:
+    # mu_0 = ||x||^2 and |mu_m| <= mu_0 (|T_m| <= 1 on the scaled spectrum)
+    assert np.allclose(mu[:, 0], n0, rtol=tol)
+    assert np.all(np.abs(mu) <= mu[:, :1] * (1 + 1e-5))
     if col0:                 # the other column blocks were zero and stay zero
         assert torch.count_nonzero(X[:, :col0]).item() == 0
