@@ -107,18 +107,23 @@ def parse():
     ap.add_argument("--tte-workload", default=None, choices=sorted(workloads.ALL),
                     help="the workload whose time to eigenpairs is measured (default: the 128x128x64 one)")
     ap.add_argument("--mode", default="filter",
-                    choices=["filter", "iteration", "batch", "fusion", "host", "sweep", "tte", "peaks"],
+                    choices=["filter", "iteration", "batch", "fusion", "host", "sweep", "tte", "peaks", "kernel"],
                     help="filter: n_b = 32 blocks of the 200x200x100 lattice at n_p = 100, plus time to "
                          "eigenpairs (default); iteration: the 64x64x32 ChebFD iteration (filter, SVQB, "
                          "Rayleigh-Ritz); batch: 64 uneven realisations, batched vs looped; fusion: fused step "
                          "vs separate SpMMV + BLAS-1 calls; host: search space in host memory vs in HBM, against "
                          "n_p; sweep: fused-filter throughput per configuration; tte: time to eigenpairs, fp64 "
                          "vs mixed policy, on --tte-workload; peaks: measured FMA rates of the fp64 and fp32 "
-                         "pipes")
+                         "pipes; kernel: filter calls on one n_b block of the 64x64x32 lattice (profiling case)")
     ap.add_argument("--host-lattice", default="64x64x32", help="host mode: lattice Nx x Ny x Nz")
     ap.add_argument("--host-n-s", type=int, default=128, help="host mode: search space width")
     ap.add_argument("--realisations", type=int, default=workloads.BATCH_COUNT)
     ap.add_argument("--prec", default="c128", choices=["c128", "c64"], help="filter arithmetic")
+    ap.add_argument("--gather", type=int, default=0,
+                    help="kernel mode: cfd_filter_opts.gather (double-word step: 16 loads X before the gathers)")
+    ap.add_argument("--arith", default="native", choices=["native", "dw"],
+                    help="complex128 filter: native fp64 arithmetic or double-word arithmetic on the fp32 pipe "
+                         "for the general steps (cfd_filter_opts.arith = 1)")
     ap.add_argument("--storage", default="packed", choices=["packed", "complex"],
                     help="matrix values as real-or-imaginary scalars (exact for Topi) or complex pairs")
     a = ap.parse_args()
@@ -349,9 +354,12 @@ def run_filter(a):
     L = b.lib()
     blocks = [b.block_of(X[:, k * n_b:(k + 1) * n_b]) for k in range(n_blocks)]
 
+    dw = prec == "c128" and a.arith == "dw"
+    opts = b.cfd_filter_opts(0, 0, 0, 0, 0, 0, 1 if dw else 0, 0)
+
     def filt(blk, npp=n_p):
-        b._check(L.cfd_filter(H.ref(), lmin, lmax, lam_l, lam_r, npp, blk, n_b, b._ptr(work), work.numel(),
-                              b._ptr(mu), b._stream()))
+        b._check(L.cfd_filter_ex(H.ref(), lmin, lmax, lam_l, lam_r, npp, blk, n_b, b._ptr(work), work.numel(),
+                                 b._ptr(mu), b.ctypes.byref(opts), b._stream()))
 
     for k in range(a.warmup):
         filt(blocks[k % n_blocks])
@@ -396,7 +404,16 @@ def run_filter(a):
     gflops = world * a.steps * n_p * model.step_flops(N, nnz, n_b) / t / 1e9
     gbs_launch = step_bytes / t_launch / 1e9
     hbm, hbm_src = measured_hbm_gbs()
-    if prec == "c128":
+    if dw:
+        kname = "k_cheb_step_dw"
+        traffic, tsrc = profiled_traffic(kname, n_b, N)
+        roof = {"bound": "hbm", "achieved": round(gbs_launch, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(gbs_launch / hbm, 4), "traffic": traffic, "traffic_source": tsrc,
+                "peak_source": hbm_src,
+                "kernel": "k_cheb_step_dw<%d,%d,moments,chunk height 32>" % (n_b, 2 if n_b >= 16 else 1),
+                "algorithmic": "nnz (16 + 4) + 5 N n_b 16 bytes per launch",
+                "avg_launch_ms": round(1e3 * t_launch, 4)}
+    elif prec == "c128":
         nominal, measured = fp64_peak(b)
         fma = model.step_fma_flops(N, nnz, n_b, packed=(a.storage == "packed"), prepared=True)
         achieved = fma / t_launch / 1e9
@@ -471,14 +488,15 @@ def run_filter(a):
                        sst, n_b, w.name, dt)}
         out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": round(1e3 * t / a.steps, 3), "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32x2" if dw else prec, "data": "synthetic",
                "config": {"workload": w.name, "lattice": list(w.lattice), "N": N, "nnz": nnz, "n_s": n_s,
                           "n_b": n_b, "n_p": n_p, "window": list(LARGE_WINDOW),
                           "bounds": [round(lmin, 6), round(lmax, 6)], "sell_C": w.sell_C,
                           "sell_sigma": w.sell_sigma, "matrix_values": a.storage,
                           "step": "one n_b block filtered with n_p fused steps and moments (block k mod %d)"
                                   % n_blocks,
-                          "filter_precision": "fp64" if prec == "c128" else "fp32 filter on fp64 block (mixed)",
+                          "filter_precision": ("fp64 storage, double-word (2 x fp32) arithmetic" if dw else "fp64")
+                                              if prec == "c128" else "fp32 filter on fp64 block (mixed)",
                           "l2": "inputs larger than L2 (X %.1f GB, work blocks %.1f GB)" % (
                               N * n_s * 16 / 1e9, 2 * N * n_b * (16 if prec == "c128" else 8) / 1e9),
                           "parallelism": "replicas" if world > 1 else "single"},
@@ -622,7 +640,8 @@ def run_iteration(a):
                           "bounds": [round(lmin, 6), round(lmax, 6)], "sell_C": w.sell_C,
                           "sell_sigma": w.sell_sigma, "matrix_values": a.storage,
                           "step": "filter (moments) + SVQB x2 + Rayleigh-Ritz",
-                          "filter_precision": "fp64" if prec == "c128" else "fp32 filter on fp64 block (mixed)",
+                          "filter_precision": ("fp64 storage, double-word (2 x fp32) arithmetic" if dw else "fp64")
+                                              if prec == "c128" else "fp32 filter on fp64 block (mixed)",
                           "l2": "inputs larger than L2 (X 1.07 GB, work blocks 0.54 GB)",
                           "parallelism": "replicas" if world > 1 else "single"},
                "gflops": round(world * a.steps * filt_flops / t / 1e9, 2),
@@ -1001,6 +1020,35 @@ def run_tte(a):
                       "time_to_eigenpairs": res}))
 
 
+def run_kernel(a):
+    """Small case for profiling one kernel: --steps filter calls of one n_b
+    block of the 64x64x32 lattice (N = 524288) with --n-p fused steps and
+    moments, after --warmup calls (complex128 with --arith, or complex64)."""
+    import torch
+    from paper_1803_02156_gb300 import binding as b, inputs
+    torch.cuda.set_device(0)
+    w = WORKLOAD
+    prec = a.prec
+    H = b.cfd_build_matrix(b.topi_params(*w.lattice, seed=w.seed), 32, 1, prec + "p")
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    X = inputs.gaussian_block_device(H.N, a.n_b, seed=w.x_seed, dtype=dt)
+    dw = prec == "c128" and a.arith == "dw"
+    ts = []
+    for r in range(a.warmup + a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.cfd_filter_ex(H, *BOUNDS, -0.3, 0.3, a.n_p, X, a.n_b, moments=True, arith=1 if dw else 0, gather=a.gather)
+        e1.record()
+        torch.cuda.synchronize()
+        if r >= a.warmup:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(ts) / a.n_p
+    print(json.dumps({"metric": "filter call, ms per step", "unit": "ms", "workload": w.name, "prec": prec,
+                      "arith": "dw" if dw else "native", "gather": a.gather, "n_b": a.n_b, "n_p": a.n_p,
+                      "ms_per_step": round(1e3 * t, 4),
+                      "model_gbs": round(model.step_bytes(H.N, H.nnz, a.n_b, prec) / t / 1e9, 1)}))
+
+
 def run_peaks(a):
     """Measured FMA rates of the fp64 and fp32 pipes (the library's probe)."""
     import torch
@@ -1031,6 +1079,8 @@ def main():
         run_tte(a)
     elif a.mode == "peaks":
         run_peaks(a)
+    elif a.mode == "kernel":
+        run_kernel(a)
     elif a.mode == "iteration":
         run_iteration(a)
     else:

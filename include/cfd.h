@@ -285,7 +285,12 @@ typedef struct cfd_filter_opts {
                              a few units of 2^-48 against 2^-53 natively), complex-double storage and memory
                              traffic unchanged; needs packed values (CFD_PACK_RI), not with persistent.
                              Results agree with arith 0 to that rounding, not bit for bit. */
-    int32_t reserved;
+    int32_t graph;        /* 1: the call's launch sequence (weights, prepared values, the n_p steps of every
+                             block, moments) is captured once as a CUDA graph on a library stream and launched
+                             as one graph on `stream`; later calls with the same arguments (pointers, sizes,
+                             bounds, window, options) on the same device replay the cached graph (up to 16
+                             are kept).  Results are bit for bit those of graph 0.  The first call of each
+                             argument set captures, so make it outside any capture of your own. */
 } cfd_filter_opts;
 
 /* cfd_filter with explicit kernel options (the autotuner's knobs besides n_b,

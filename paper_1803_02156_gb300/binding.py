@@ -65,7 +65,7 @@ class cfd_block(ctypes.Structure):
 class cfd_filter_opts(ctypes.Structure):
     _fields_ = [("vpt", ctypes.c_int32), ("grid_cap", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("staged", ctypes.c_int32), ("gather", ctypes.c_int32),
-                ("fixed_chunk", ctypes.c_int32), ("arith", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fixed_chunk", ctypes.c_int32), ("arith", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
 class cfd_solve_params(ctypes.Structure):
@@ -342,18 +342,19 @@ def cfd_filter(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=Non
 
 
 def cfd_filter_ex(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, vpt=0, grid_cap=0, moments=False, work=None,
-                  stream=None, persistent=0, staged=0, gather=0, fixed_chunk=0, arith=0):
+                  stream=None, persistent=0, staged=0, gather=0, fixed_chunk=0, arith=0, graph=0):
     """cfd_filter with the kernel options (vectors per thread, CTA cap, persistent
     launch, TMA staging: 1 on, -1 off, 0 default; gathers in flight per row in
     staged steps: 16 all at once, 4 groups of four, 0 default; fixed_chunk -1:
     generic staged kernel instead of the one compiled for C = 32; arith 1:
-    complex-double general steps in double-word arithmetic on the fp32 pipe)."""
+    complex-double general steps in double-word arithmetic on the fp32 pipe;
+    graph 1: the call captured once as a CUDA graph and replayed)."""
     blk = block_of(X)
     ws = cfd_filter_workspace(H.N, blk.n_cols, n_b, n_p, H.prec, blk.prec)
     if work is None or work.numel() < ws:
         work = _workspace(ws, X.device)
     mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=X.device) if moments else None
-    o = cfd_filter_opts(vpt, grid_cap, persistent, staged, gather, fixed_chunk, arith)
+    o = cfd_filter_opts(vpt, grid_cap, persistent, staged, gather, fixed_chunk, arith, graph)
     _check(lib().cfd_filter_ex(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
                                _ptr(mu), ctypes.byref(o), _stream(stream)))
     return mu
@@ -471,14 +472,15 @@ def cfd_build_batch(params_list, C=32, sigma=1, prec="c128", device="cuda", stre
     return Batch(out, bufs, list(params_list), rid, off)
 
 
-def cfd_filter_batched(B, windows, n_p, X, n_b, persistent=0, vpt=0, work=None, stream=None):
+def cfd_filter_batched(B, windows, n_p, X, n_b, persistent=0, vpt=0, work=None, stream=None, graph=0, arith=0):
     """Filter every realisation of batch B at once; windows: float64 device tensor [R, 4]
-    (lmin, lmax, lam_l, lam_r per realisation)."""
+    (lmin, lmax, lam_l, lam_r per realisation); graph 1: captured once as a CUDA
+    graph and replayed; arith 1: double-word general steps (complex double)."""
     blk = block_of(X)
     ws = lib().cfd_filter_batched_workspace(B.N, B.R, blk.n_cols, n_b, n_p, B.prec, blk.prec)
     if work is None or work.numel() < ws:
         work = _workspace(ws, X.device)
-    o = cfd_filter_opts(vpt, 0, persistent)
+    o = cfd_filter_opts(vpt, 0, persistent, 0, 0, 0, arith, graph)
     _check(lib().cfd_filter_batched(B.ref(), _ptr(B.chunk_rid), B.R, _ptr(windows), n_p, blk, n_b, _ptr(work),
                                     work.numel(), ctypes.byref(o), _stream(stream)))
 

@@ -12,6 +12,8 @@ static thread_local char g_last_error[512] = {0};
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 cfd_status fail(cfd_status st, const char *fmt, ...) {
     va_list ap;

@@ -40,6 +40,9 @@ void clear_error();
 
 // Every kernel the library launches is counted (cfd_launch_count()).
 void count_launch();
+// Adds n (negative: removes) kernels to the count; the current count.
+void count_launches(long long n);
+unsigned long long launch_count();
 #define CFD_COUNT_LAUNCH() ::cfd::count_launch()
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -2,6 +2,7 @@
 // fused SELL-C-sigma SpMMV kernel per recurrence step (the paper's
 // chebfd_op), weights table, moment finalisation, precision conversion.
 #include <algorithm>
+#include <cstring>
 #include <cooperative_groups.h>
 #include <type_traits>
 
@@ -308,12 +309,15 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
     A.fixed_chunk = P.fixed_chunk;
     A.status = ws.status;
     const bool dw = std::is_same<T, double>::value && P.arith == ARITH_DW;
+    // persistent general steps with the staged chunk loop (packed values);
+    // the unstaged persistent kernel runs all steps in one launch
+    const bool pstaged = P.persistent && P.staged && A.H.packed;
     if (dw) {
         // double-word general steps: 2 alpha (H - beta) as {hi, lo} float pairs
         CFD_TRY(launch_prepare_values_dw(H, P.alpha, P.beta, P.chunk_rid, P.rcoef, P.rcoef_ld, ws.prep,
                                          ws.prep_bytes, stream));
         A.prep_val = ws.prep;
-    } else if (P.staged && !P.persistent) {
+    } else if (P.staged && (!P.persistent || pstaged)) {
         // the staged general steps read 2 alpha (H - beta), prepared once per call
         CFD_TRY(launch_prepare_values(H, P.alpha, P.beta, P.chunk_rid, P.rcoef, P.rcoef_ld, ws.prep, ws.prep_bytes,
                                       stream));
@@ -335,7 +339,16 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
             xb = reinterpret_cast<C *>(xsrc);
             ldx = X.ld;
         }
-        if (P.persistent) {
+        if (pstaged) {
+            // steps 1 and 2 as single launches, then steps 3..n_p in one
+            // cooperative launch
+            A.dots = nullptr;
+            A.vin = xb; A.ldin = ldx; A.w = va; A.ldw = n_b; A.x = nullptr; A.ldx = 0; A.a = P.alpha; A.p = 1;
+            CFD_TRY(launch_step<T>(STEP_FIRST, n_b, vpt, A, P.grid_cap, stream));
+            A.vin = va; A.ldin = n_b; A.w = vb; A.ldw = n_b; A.x = xb; A.ldx = ldx; A.a = 2.0 * P.alpha; A.p = 2;
+            CFD_TRY(launch_step<T>(STEP_SECOND, n_b, vpt, A, P.grid_cap, stream));
+            if (n_p >= 3) CFD_TRY(launch_persistent_staged<T>(n_b, vpt, A, va, vb, n_p, P.grid_cap, stream));
+        } else if (P.persistent) {
             // all n_p steps of this block in one cooperative launch
             A.a = P.alpha;
             A.dots = nullptr;
@@ -415,7 +428,7 @@ static FilterScratch carve_filter(const cfd_matrix *H, const cfd_block &X, int n
 cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
                             const cfd_block &X, int n_b, int vpt, int grid_cap, int persistent, int staged,
                             void *work, size_t work_bytes, double *moments, cudaStream_t stream, int gather,
-                            int fixed_chunk, int arith) {
+                            int fixed_chunk, int arith, int graph) {
     CFD_TRY(check_filter_args(H, n_p, X, n_b, vpt));
     if (arith != ARITH_NATIVE && arith != ARITH_DW) return fail(CFD_ERR_ARG, "arith=%d not in {0, 1}", arith);
     if (arith == ARITH_DW) {
@@ -425,6 +438,7 @@ cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, doubl
             return fail(CFD_ERR_ARG, "double-word arithmetic needs packed matrix values (CFD_PACK_RI)");
         if (persistent) return fail(CFD_ERR_ARG, "the persistent filter has no double-word variant");
     }
+    if (graph != 0 && graph != 1) return fail(CFD_ERR_ARG, "graph=%d not in {0, 1}", graph);
     if (!(lmin < lmax) || !(lmin <= lam_l && lam_l < lam_r && lam_r <= lmax))
         return fail(CFD_ERR_ARG, "need lmin <= lam_l < lam_r <= lmax (got %g %g %g %g)", lmin, lam_l, lam_r, lmax);
     if (persistent && moments) return fail(CFD_ERR_ARG, "the persistent filter records no moments");
@@ -433,8 +447,6 @@ cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, doubl
     if (work_bytes < need) return fail(CFD_ERR_OOM, "filter workspace %zu < %zu bytes", work_bytes, need);
     if (!aligned16(work)) return fail(CFD_ERR_ARG, "work must be 16-byte aligned");
     FilterScratch ws = carve_filter(H, X, n_b, n_p, work, work_bytes);
-    CFD_CUDA(cudaMemsetAsync(ws.ticket, 0, sizeof(unsigned), stream));
-    CFD_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), stream));
     FilterPlan P;
     P.n_b = n_b;
     P.n_p = n_p;
@@ -447,9 +459,31 @@ cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, doubl
     P.arith = arith;
     P.alpha = 2.0 / (lmax - lmin);
     P.beta = 0.5 * (lmax + lmin);
-    CFD_TRY(launch_filter_coeffs(P.alpha, P.beta, lam_l, lam_r, n_p, ws.gc, stream));
-    if (H->prec == CFD_C128) return run_filter<double>(H, P, X, ws, moments, stream);
-    return run_filter<float>(H, P, X, ws, moments, stream);
+    auto enqueue = [&](cudaStream_t s) -> cfd_status {
+        CFD_CUDA(cudaMemsetAsync(ws.ticket, 0, sizeof(unsigned), s));
+        CFD_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+        CFD_TRY(launch_filter_coeffs(P.alpha, P.beta, lam_l, lam_r, n_p, ws.gc, s));
+        if (H->prec == CFD_C128) return run_filter<double>(H, P, X, ws, moments, s);
+        return run_filter<float>(H, P, X, ws, moments, s);
+    };
+    if (!graph) return enqueue(stream);
+    // every argument that shapes the launch sequence or its parameters
+    struct Key {
+        cfd_matrix H;
+        cfd_block X;
+        double lmin, lmax, lam_l, lam_r;
+        const void *work, *moments;
+        size_t work_bytes;
+        int n_p, n_b, vpt, grid_cap, persistent, staged, gather, fixed_chunk, arith, kind;
+    } key;
+    std::memset(&key, 0, sizeof(key));
+    key.H = *H;
+    key.X = X;
+    key.lmin = lmin; key.lmax = lmax; key.lam_l = lam_l; key.lam_r = lam_r;
+    key.work = work; key.moments = moments; key.work_bytes = work_bytes;
+    key.n_p = n_p; key.n_b = n_b; key.vpt = P.vpt; key.grid_cap = P.grid_cap; key.persistent = persistent;
+    key.staged = P.staged; key.gather = P.gather; key.fixed_chunk = fixed_chunk; key.arith = arith; key.kind = 1;
+    return run_as_graph(&key, sizeof(key), stream, enqueue);
 }
 
 cfd_status filter_impl(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
@@ -533,10 +567,16 @@ size_t batched_workspace(int64_t N, int R, int n_s, int n_b, int n_p, int prec_H
 
 cfd_status filter_batched_impl(const cfd_matrix *H, const int32_t *chunk_rid, int R, const double *windows, int n_p,
                                const cfd_block &X, int n_b, int vpt, int persistent, void *work, size_t work_bytes,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, int arith, int graph) {
     CFD_TRY(check_filter_args(H, n_p, X, n_b, vpt));
     if (!chunk_rid || !windows || R < 1) return fail(CFD_ERR_ARG, "batch description missing");
     if (!work) return fail(CFD_ERR_ARG, "work is NULL");
+    if (arith != ARITH_NATIVE && arith != ARITH_DW) return fail(CFD_ERR_ARG, "arith=%d not in {0, 1}", arith);
+    if (arith == ARITH_DW && (H->prec != CFD_C128 || X.prec != CFD_C128 || !(H->flags & CFD_MATRIX_PACKED) ||
+                              persistent))
+        return fail(CFD_ERR_ARG, "double-word arithmetic needs a packed complex-double batch and block, "
+                                 "without the persistent launch");
+    if (graph != 0 && graph != 1) return fail(CFD_ERR_ARG, "graph=%d not in {0, 1}", graph);
     size_t need = batched_workspace(H->n_rows, R, X.n_cols, n_b, n_p, H->prec, X.prec);
     if (work_bytes < need) return fail(CFD_ERR_OOM, "batched filter workspace %zu < %zu bytes", work_bytes, need);
     if (!aligned16(work)) return fail(CFD_ERR_ARG, "work must be 16-byte aligned");
@@ -544,11 +584,6 @@ cfd_status filter_batched_impl(const cfd_matrix *H, const int32_t *chunk_rid, in
     FilterScratch ws = carve_filter(H, X, n_b, n_p, work, base);
     double *rcoef = reinterpret_cast<double *>(static_cast<char *>(work) + base);
     int64_t ld = n_p + 3;
-    CFD_CUDA(cudaMemsetAsync(ws.ticket, 0, sizeof(unsigned), stream));
-    CFD_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), stream));
-    k_batch_coeffs<<<(unsigned)((R * ld + 127) / 128), 128, 0, stream>>>(windows, R, n_p, rcoef);
-    CFD_COUNT_LAUNCH();
-    CFD_LAUNCH_CHECK();
     FilterPlan P;
     P.n_b = n_b;
     P.n_p = n_p;
@@ -562,8 +597,31 @@ cfd_status filter_batched_impl(const cfd_matrix *H, const int32_t *chunk_rid, in
     P.rcoef_ld = ld;
     P.staged = (int)default_staged(H->prec);
     P.gather = default_gather(H->prec);
-    if (H->prec == CFD_C128) return run_filter<double>(H, P, X, ws, nullptr, stream);
-    return run_filter<float>(H, P, X, ws, nullptr, stream);
+    P.arith = arith;
+    auto enqueue = [&](cudaStream_t s) -> cfd_status {
+        CFD_CUDA(cudaMemsetAsync(ws.ticket, 0, sizeof(unsigned), s));
+        CFD_CUDA(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+        k_batch_coeffs<<<(unsigned)((R * ld + 127) / 128), 128, 0, s>>>(windows, R, n_p, rcoef);
+        CFD_COUNT_LAUNCH();
+        CFD_LAUNCH_CHECK();
+        if (H->prec == CFD_C128) return run_filter<double>(H, P, X, ws, nullptr, s);
+        return run_filter<float>(H, P, X, ws, nullptr, s);
+    };
+    if (!graph) return enqueue(stream);
+    struct Key {
+        cfd_matrix H;
+        cfd_block X;
+        const void *chunk_rid, *windows, *work;
+        size_t work_bytes;
+        int R, n_p, n_b, vpt, persistent, arith, kind;
+    } key;
+    std::memset(&key, 0, sizeof(key));
+    key.H = *H;
+    key.X = X;
+    key.chunk_rid = chunk_rid; key.windows = windows; key.work = work; key.work_bytes = work_bytes;
+    key.R = R; key.n_p = n_p; key.n_b = n_b; key.vpt = P.vpt; key.persistent = persistent; key.arith = arith;
+    key.kind = 2;
+    return run_as_graph(&key, sizeof(key), stream, enqueue);
 }
 
 }  // namespace cfd
@@ -603,12 +661,13 @@ cfd_status cfd_filter_ex(const cfd_matrix *H, double lmin, double lmax, double l
     int gather = opts ? opts->gather : 0;
     int fixed_chunk = opts ? opts->fixed_chunk : 0;
     int arith = opts ? opts->arith : 0;
+    int graph = opts ? opts->graph : 0;
     if (cap < 0) return fail(CFD_ERR_ARG, "grid_cap < 0");
     if (staged < -1 || staged > 2) return fail(CFD_ERR_ARG, "staged=%d not in -1..2", staged);
     if (gather != 0 && gather != 4 && gather != 8 && gather != STEP_GATHER_ALL)
         return fail(CFD_ERR_ARG, "gather=%d not in {0, 4, 8, %d}", gather, STEP_GATHER_ALL);
     return filter_impl_opts(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, vpt, cap, pers, staged, work, work_bytes,
-                            moments, stream, gather, fixed_chunk, arith);
+                            moments, stream, gather, fixed_chunk, arith, graph);
 }
 
 cfd_status cfd_kpm_moments(const cfd_matrix *H, double lmin, double lmax, int n_p, cfd_block R, int n_b, void *work,
@@ -644,7 +703,9 @@ cfd_status cfd_filter_batched(const cfd_matrix *H, const int32_t *chunk_rid, int
                               cudaStream_t stream) {
     clear_error();
     int vpt = opts ? opts->vpt : 0, pers = opts ? opts->persistent : 0;
-    return filter_batched_impl(H, chunk_rid, R, windows, n_p, X, n_b, vpt, pers, work, work_bytes, stream);
+    int arith = opts ? opts->arith : 0, graph = opts ? opts->graph : 0;
+    return filter_batched_impl(H, chunk_rid, R, windows, n_p, X, n_b, vpt, pers, work, work_bytes, stream, arith,
+                               graph);
 }
 
 }  // extern "C"

@@ -3,6 +3,8 @@
 // alpha = 1, beta = 0).
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace cfd {
@@ -73,6 +75,12 @@ cfd_status launch_persistent_p(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> 
 template <typename T>
 cfd_status launch_persistent(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> *xb,
                              int64_t ldx, int n_p, int grid_cap, cudaStream_t stream);
+// General steps 3..n_p of one block in one cooperative launch with the
+// TMA-staged chunk loop (packed values prepared in A.prep_val; A.x, A.ldx the
+// block; steps 1 and 2 run before it).  Instantiated in step_f*_packed.cu.
+template <typename T>
+cfd_status launch_persistent_staged(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, int n_p,
+                                    int grid_cap, cudaStream_t s);
 
 // Complex-double general steps in double-word arithmetic on the fp32 pipe
 // (step_dw.cu): the step for general step p (last: X written back as
@@ -83,6 +91,12 @@ cfd_status launch_dw_convert(void *p, int64_t ld, int64_t n_rows, int nb, bool t
 cfd_status launch_prepare_values_dw(const cfd_matrix *H, double alpha, double beta, const int32_t *chunk_rid,
                                     const double *rcoef, int64_t rcoef_ld, void *out, size_t out_bytes,
                                     cudaStream_t stream);
+
+// Runs body(s) captured as a CUDA graph on a library stream and launches the
+// graph on `stream`; later calls with the same key bytes (on the same device)
+// replay the cached executable without capturing again (graph.cu).
+cfd_status run_as_graph(const void *key, size_t key_bytes, cudaStream_t stream,
+                        const std::function<cfd_status(cudaStream_t)> &body);
 
 // Arithmetic of the complex-double filter's general steps.
 enum FilterArith : int { ARITH_NATIVE = 0, ARITH_DW = 1 };
@@ -149,13 +163,13 @@ cfd_status launch_widen(const float2 *src, int64_t lds, double2 *dst, int64_t ld
 cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
                             const cfd_block &X, int n_b, int vpt, int grid_cap, int persistent, int staged,
                             void *work, size_t work_bytes, double *moments, cudaStream_t stream, int gather = 0,
-                            int fixed_chunk = 0, int arith = ARITH_NATIVE);
+                            int fixed_chunk = 0, int arith = ARITH_NATIVE, int graph = 0);
 size_t batched_workspace(int64_t N, int R, int n_s, int n_b, int n_p, int prec_H, int prec_X);
 cfd_status kpm_impl(const cfd_matrix *H, double lmin, double lmax, int n_p, const cfd_block &R, int n_b,
                     void *work, size_t work_bytes, double *moments, cudaStream_t stream);
 cfd_status filter_batched_impl(const cfd_matrix *H, const int32_t *chunk_rid, int R, const double *windows, int n_p,
                                const cfd_block &X, int n_b, int vpt, int persistent, void *work, size_t work_bytes,
-                               cudaStream_t stream);
+                               cudaStream_t stream, int arith = ARITH_NATIVE, int graph = 0);
 // The whole filter with explicit tuning knobs (vpt <= 0: default; grid_cap <= 0: none).
 cfd_status filter_impl(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
                        int n_p, const cfd_block &X, int n_b, int vpt, int grid_cap, void *work,

@@ -196,6 +196,99 @@ cfd_status rayleigh_ritz_impl(const cfd_matrix *H, const cfd_block &X, double *e
     return CFD_OK;
 }
 
+// SVQB's second pass folded into Rayleigh-Ritz (the restart step of the
+// solve): after the first pass X1 = X0 M1, the second pass would form
+// X2 = X1 M2 and Rayleigh-Ritz then Z = H X2, G = X2^H Z.  With Z1 = H X1 and
+// G1 = X1^H Z1 instead, H X2 = Z1 M2 and X2^H H X2 = M2^H G1 M2, so
+// X <- X1 (M2 Y), Z <- Z1 (M2 Y) give the same Ritz pairs with one N x n x n
+// product fewer (three Grams and three projections instead of four).
+// Everything else as orthogonalize_impl followed by rayleigh_ritz_impl;
+// rank_dev (nullable) receives the first pass's rank, and when e_mid is
+// given it is recorded after the first pass.
+size_t orth_rr_workspace(int64_t N, int n) {
+    Carve c(nullptr, 0);
+    c.take<int>(64);
+    c.take<char>(svqb_workspace(N, n));
+    c.take<double2>((size_t)N * n);        // Z
+    c.take<double2>((size_t)2 * n * n);    // S2, S2~
+    c.take<double2>((size_t)n * n);        // Q
+    c.take<double2>((size_t)n * n);        // M2, then M2 Y
+    c.take<double2>((size_t)n * n);        // G1
+    c.take<double2>((size_t)n * n);        // T = G1 M2
+    c.take<double2>((size_t)n * n);        // G = M2^H T
+    c.take<double2>((size_t)n * n);        // Y
+    c.take<double>((size_t)n);             // theta
+    c.take<double>((size_t)n);             // d
+    c.take<double>((size_t)STEP_MAX_GRID * 2 * 64);
+    c.take<unsigned>(64);
+    c.take<char>(gram_workspace(N, n, n));
+    c.take<char>(project_workspace(n, n));
+    c.take<char>(eigh_workspace(n));
+    c.take<char>(resid_workspace(n));
+    return round_up(c.off, 256);
+}
+
+cfd_status orth_rr_impl(const cfd_matrix *H, const cfd_block &X, double tol, int *rank_dev, double *evals,
+                        double *resid, void *work, size_t work_bytes, cudaEvent_t e_mid, cudaStream_t stream) {
+    CFD_TRY(check_matrix(H));
+    CFD_TRY(check_c128_block(X));
+    if (H->prec != CFD_C128) return fail(CFD_ERR_ARG, "Rayleigh-Ritz needs the complex-double matrix");
+    if (X.n_rows != H->n_rows) return fail(CFD_ERR_ARG, "block rows do not match the matrix");
+    if (!evals || !work) return fail(CFD_ERR_ARG, "evals or work is NULL");
+    const int64_t N = X.n_rows;
+    const int n = X.n_cols;
+    if (work_bytes < orth_rr_workspace(N, n)) return fail(CFD_ERR_OOM, "orthogonalisation workspace too small");
+    const double tau = tol > 0 ? tol : 1e-14;
+    Carve c(work, work_bytes);
+    int *r1 = c.take<int>(64);
+    const size_t svqb_bytes = svqb_workspace(N, n);
+    char *sw = c.take<char>(svqb_bytes);
+    double2 *Z = c.take<double2>((size_t)N * n);
+    double2 *S = c.take<double2>((size_t)2 * n * n);
+    double2 *Q = c.take<double2>((size_t)n * n);
+    double2 *M = c.take<double2>((size_t)n * n);
+    double2 *G1 = c.take<double2>((size_t)n * n);
+    double2 *T = c.take<double2>((size_t)n * n);
+    double2 *G = c.take<double2>((size_t)n * n);
+    double2 *Y = c.take<double2>((size_t)n * n);
+    double *theta = c.take<double>((size_t)n);
+    double *d = c.take<double>((size_t)n);
+    double *partial = c.take<double>((size_t)STEP_MAX_GRID * 2 * 64);
+    unsigned *ticket = c.take<unsigned>(64);
+    double *gw = reinterpret_cast<double *>(c.take<char>(gram_workspace(N, n, n)));
+    double *pw = reinterpret_cast<double *>(c.take<char>(project_workspace(n, n)));
+    const size_t ewb = eigh_workspace(n);
+    void *ew = c.take<char>(ewb);
+    double *rw = reinterpret_cast<double *>(c.take<char>(resid_workspace(n)));
+    double2 *Xp = static_cast<double2 *>(X.ptr);
+    // first pass: X1 = X0 M1
+    CFD_TRY(svqb_pass(Xp, X.ld, N, n, tau, sw, svqb_bytes, rank_dev ? rank_dev : r1, stream));
+    if (e_mid) CFD_CUDA(cudaEventRecord(e_mid, stream));
+    // Z1 = H X1, S2 = X1^H X1, G1 = X1^H Z1
+    CFD_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), stream));
+    CFD_TRY(spmmv_block(H, Xp, X.ld, Z, n, n, partial, ticket, nullptr, stream));
+    CFD_TRY(gram(Xp, X.ld, n, Xp, X.ld, n, N, S, n, gw, stream, true));
+    CFD_TRY(gram(Xp, X.ld, n, Z, n, n, N, G1, n, gw, stream, true));
+    // second pass's coefficients M2 = D Q Theta^{-1/2} from S2
+    k_svqb_scale<<<(n * n + 255) / 256, 256, 0, stream>>>(S, n, d);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    CFD_TRY(eigh(S + (size_t)n * n, n, n, theta, Q, n, ew, ewb, stream, nullptr));
+    k_svqb_coeff<<<(n * n + 255) / 256, 256, 0, stream>>>(Q, theta, d, n, tau, M, r1 + 32);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    // G = M2^H G1 M2 (G1 Hermitian: G1^H M2 = G1 M2), its eigenvectors Y
+    CFD_TRY(gram(G1, n, n, M, n, n, n, T, n, gw, stream));
+    CFD_TRY(gram(M, n, n, T, n, n, n, G, n, gw, stream));
+    CFD_TRY(eigh(G, n, n, evals, Y, n, ew, ewb, stream, nullptr));
+    // W = M2 Y; X <- X1 W, Z <- Z1 W; residual norms
+    CFD_TRY(project_inplace(M, n, n, n, Y, n, n, pw, stream));
+    CFD_TRY(project_inplace(Xp, X.ld, N, n, M, n, n, pw, stream));
+    CFD_TRY(project_inplace(Z, n, N, n, M, n, n, pw, stream));
+    if (resid) CFD_TRY(resid_norms(Z, n, Xp, X.ld, evals, n, N, resid, rw, stream));
+    return CFD_OK;
+}
+
 }  // namespace cfd
 
 using namespace cfd;

@@ -15,6 +15,9 @@ size_t orthogonalize_workspace(int64_t N, int n);
 cfd_status orthogonalize_impl(const cfd_block &X, double tol, int *rank_host, int *rank_dev, void *work,
                               size_t work_bytes, cudaStream_t stream);
 size_t rr_workspace(int64_t N, int n);
+size_t orth_rr_workspace(int64_t N, int n);
+cfd_status orth_rr_impl(const cfd_matrix *H, const cfd_block &X, double tol, int *rank_dev, double *evals,
+                        double *resid, void *work, size_t work_bytes, cudaEvent_t e_mid, cudaStream_t stream);
 cfd_status rayleigh_ritz_impl(const cfd_matrix *H, const cfd_block &X, double *evals, double *resid, void *work,
                               size_t work_bytes, cudaStream_t stream);
 size_t bounds_workspace(int64_t N, int steps);
@@ -35,7 +38,7 @@ SolveWs solve_ws(const cfd_matrix *H, const cfd_matrix *Hl, const cfd_solve_para
     w.filt = filter_workspace(N, p->n_s, p->n_b, p->n_p, CFD_C128, CFD_C128);
     if (Hl) w.filt = std::max(w.filt, filter_workspace(N, p->n_s, p->n_b, p->n_p, CFD_C64, CFD_C128));
     w.orth = orthogonalize_workspace(N, p->n_s) + 256;
-    w.rr = rr_workspace(N, p->n_s);
+    w.rr = std::max(rr_workspace(N, p->n_s), orth_rr_workspace(N, p->n_s));
     w.bnd = bounds_workspace(N, std::max(2, p->bounds_steps > 0 ? p->bounds_steps : 40)) + 256;
     // phases run one after another: the scratch is shared
     w.total = round_up(std::max(std::max(w.filt, w.orth), std::max(w.rr, w.bnd)), 256) + 8192;
@@ -128,10 +131,10 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
                                  (dw && !tr.low) ? ARITH_DW : ARITH_NATIVE));
         cudaEventRecord(e1, stream);
         int rank = n;
-        CFD_TRY(orthogonalize_impl(X, 1e-14, nullptr, reinterpret_cast<int *>(small + 8), scratch, scratch_bytes,
-                                   stream));
-        cudaEventRecord(e2, stream);
-        CFD_TRY(rayleigh_ritz_impl(H, X, ev_dev, rs_dev, scratch, scratch_bytes, stream));
+        // SVQB's first pass (t_orth), then its second pass folded into
+        // Rayleigh-Ritz (t_rr)
+        CFD_TRY(orth_rr_impl(H, X, 1e-14, reinterpret_cast<int *>(small + 8), ev_dev, rs_dev, scratch, scratch_bytes,
+                             e2, stream));
         cudaEventRecord(e3, stream);
         CFD_CUDA(cudaMemcpyAsync(evals, ev_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaMemcpyAsync(resid, rs_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));

@@ -7,4 +7,7 @@ template cfd_status launch_step_p<double, true>(int, int, int, const StepArgs<do
 template cfd_status launch_persistent_p<double, true>(int, int, const StepArgs<double> &, cplx_t<double> *, cplx_t<double> *,
                                                   cplx_t<double> *, int64_t, int, int, cudaStream_t);
 
+template cfd_status launch_persistent_staged<double>(int, int, const StepArgs<double> &, cplx_t<double> *, cplx_t<double> *, int,
+                                                   int, cudaStream_t);
+
 }  // namespace cfd

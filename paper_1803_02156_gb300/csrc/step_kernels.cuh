@@ -776,6 +776,143 @@ k_cheb_persistent(const StepArgs<T> A0, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> 
     }
 }
 
+// General steps 3..n_p of one block in a single cooperative launch, each step
+// the TMA-staged chunk loop of k_cheb_step_staged (packed values prepared as
+// 2 alpha (H - beta), A.prep_val), the grid synchronising between steps
+// (every step gathers V_cur rows other CTAs wrote in the previous one).
+// Steps 1 and 2 are launched before it, so the kernel holds only the general
+// step's registers.  A CTA keeps the same chunks in every step, and the copy
+// of its first chunk of step p + 1 is issued while it computes its last chunk
+// of step p.  No moments.  A bounded wait that expires records
+// CFD_ERR_TIMEOUT in *A.status; the CTA drains its copies and still meets
+// every grid barrier, and after the barrier all CTAs see the status and
+// return together (no CTA waits at a barrier another has left).
+template <typename T, int NB, int VPT, int CH>
+__global__ void __launch_bounds__(STEP_WARPS * 32, sizeof(T) == 4 ? 5 : 3)
+k_cheb_persistent_staged(const StepArgs<T> A0, cplx_t<T> *va, cplx_t<T> *vb, int n_p, int slots_cap) {
+    cg::grid_group grid = cg::this_grid();
+    constexpr int TPR = NB / VPT;
+    constexpr int RPW = 32 / TPR;
+    using V = T;                                  // packed values
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_len[2];
+    const int col_bytes = (int)round_up_dev((size_t)slots_cap * 4, 16);
+    auto col_s = [&](int b) { return reinterpret_cast<int32_t *>(smem_raw + b * col_bytes); };
+    auto val_s = [&](int b) {
+        return reinterpret_cast<V *>(smem_raw + 2 * col_bytes + (size_t)b * slots_cap * sizeof(V));
+    };
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int sub = lane / TPR;
+    const int j0 = (lane % TPR) * VPT;
+    const int log2C = CH > 0 ? __ffs(CH) - 1 : A0.H.log2C;
+    const int chunk_h = CH > 0 ? CH : 1 << log2C;
+    const int64_t n_rows = A0.H.n_rows;
+    const int64_t n_chunks = (n_rows + chunk_h - 1) >> log2C;
+    const V *gval = reinterpret_cast<const V *>(A0.prep_val);
+    const uint32_t tx_extra = A0.staged == 2 ? 16u : 0u;
+    const long long limit = A0.staged == 2 ? (1LL << 24) : (1LL << 32);
+    MomentAcc<T> uu[VPT], wu[VPT];                // unused (no moments)
+    volatile int *status = A0.status;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int64_t c, int b) {
+        const int cl = __ldg(A0.H.chunk_len + c);
+        const int len = (cl & 0xffff) + (cl >> 16);
+        const int64_t base = __ldg(A0.H.chunk_ptr + c);
+        const uint32_t nslot = (uint32_t)len << log2C;
+        s_len[b] = cl;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[b], nslot * (uint32_t)(4 + sizeof(V)) + tx_extra);
+        if (nslot) {
+            tma_load_1d(col_s(b), A0.H.col + base, nslot * 4u, &bar[b]);
+            tma_load_1d(val_s(b), gval + base, nslot * (uint32_t)sizeof(V), &bar[b]);
+        }
+    };
+    const bool has_work = (int64_t)blockIdx.x < n_chunks;
+    int k = 0;                     // chunk iterations over all steps (buffer k & 1, phase (k >> 1) & 1)
+    bool in_flight = false;        // a copy for iteration k was issued and not yet waited for
+    if (tid == 0 && has_work) issue(blockIdx.x, 0);
+    in_flight = has_work;
+    __syncthreads();
+    StepArgs<T> A = A0;
+    for (int p = 3; p <= n_p; ++p) {
+        A.vin = (p & 1) ? vb : va;
+        A.ldin = NB;
+        A.w = (p & 1) ? va : vb;
+        A.ldw = NB;
+        A.p = p;
+        StepCoef<T, STEP_GENERAL> cf;
+        cf.init(A);
+        bool ok = true;
+        bool issued_next = false;  // the copy for iteration k + 1 was issued
+        for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++k) {
+            const int b = k & 1;
+            // the next chunk: of this step, else this CTA's first of the next step
+            int64_t cn = c + gridDim.x;
+            issued_next = true;
+            if (cn >= n_chunks) {
+                cn = blockIdx.x;
+                issued_next = p < n_p;
+            }
+            if (tid == 0 && issued_next) issue(cn, b ^ 1);
+            const bool landed = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);
+            if (landed) {
+                const int cl = s_len[b];
+                const int nre = cl & 0xffff;
+                const int len = nre + (cl >> 16);
+                cf.for_chunk(A, c);
+                for (int rr = warp * RPW + sub; rr < chunk_h; rr += STEP_WARPS * RPW) {
+                    const int64_t r = (c << log2C) + rr;
+                    if (r >= n_rows) continue;
+                    const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
+                    process_row<T, NB, VPT, STEP_GENERAL, false, true, true, 0, CH, true>(
+                        A, i, col_s(b) + rr, val_s(b) + rr, log2C, nre, len, j0, cf, uu, wu);
+                }
+            }
+            if (!__syncthreads_and(landed)) {
+                ok = false;
+                break;
+            }
+            in_flight = issued_next;
+        }
+        if (!ok) {
+            in_flight = false;
+            if (tid == 0) {
+                // drain: the copy of iteration k (not landed) and, if issued, of k + 1
+                const int b = k & 1;
+                if (tx_extra) {
+                    mbar_complete_tx(&bar[b], tx_extra);
+                    if (issued_next) mbar_complete_tx(&bar[b ^ 1], tx_extra);
+                }
+                const long long drain_limit = 1LL << 32;
+                bool drained = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), drain_limit);
+                if (issued_next)
+                    drained = mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1), drain_limit) && drained;
+                atomicOr(A0.status, drained ? (int)CFD_ERR_TIMEOUT : (int)CFD_ERR_TIMEOUT | CFD_STATUS_DRAIN_EXPIRED);
+            }
+        }
+        grid.sync();
+        if (*status != 0) {
+            // every CTA leaves here, after the same barrier; one that did not
+            // fail may still have the copy of its next chunk in flight
+            if (tid == 0 && in_flight) {
+                const int b = k & 1;
+                if (tx_extra) mbar_complete_tx(&bar[b], tx_extra);
+                if (!mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), 1LL << 32))
+                    atomicOr(A0.status, (int)CFD_ERR_TIMEOUT | CFD_STATUS_DRAIN_EXPIRED);
+            }
+            return;
+        }
+    }
+}
+
 // --------------------------------------------------------- launching --
 
 namespace {
@@ -935,6 +1072,86 @@ cfd_status launch_persistent_nbp(const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> 
 }
 
 }  // namespace
+
+namespace {
+
+template <typename T, int NB, int VPT, int CH>
+cfd_status launch_persistent_staged_nb(const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, int n_p, int grid_cap,
+                                       cudaStream_t stream) {
+    const int slots_cap = A.H.slots_bound << A.H.log2C;
+    if (slots_cap <= 0) return fail(CFD_ERR_ARG, "matrix has no slot bound; cannot stage");
+    const size_t smem = 2 * round_up((size_t)slots_cap * 4, 16) + round_up(2 * (size_t)slots_cap * sizeof(T), 16);
+    if (smem > 200 * 1024) return fail(CFD_ERR_ARG, "chunk too large to stage (%zu bytes)", smem);
+    auto kern = k_cheb_persistent_staged<T, NB, VPT, CH>;
+    struct Cache {
+        std::mutex mu;
+        int occ[64];
+        size_t occ_smem[64];
+        size_t attr_smem[64];
+    };
+    static Cache cache{};
+    int dev = 0;
+    CFD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CFD_ERR_ARG, "device ordinal %d out of range", dev);
+    int resident = 0;
+    {
+        std::lock_guard<std::mutex> lock(cache.mu);
+        if (smem > cache.attr_smem[dev]) {
+            CFD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            cache.attr_smem[dev] = smem;
+        }
+        if (cache.occ[dev] == 0 || cache.occ_smem[dev] != smem) {
+            int o = 0;
+            CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, STEP_WARPS * 32, smem));
+            if (o < 1) return fail(CFD_ERR_ARG, "persistent staged step does not fit on an SM");
+            cache.occ[dev] = std::min(o, STEP_MAX_CTAS_PER_SM);
+            cache.occ_smem[dev] = smem;
+        }
+        resident = cache.occ[dev];
+    }
+    const int64_t n_chunks = (A.H.n_rows + (1LL << A.H.log2C) - 1) >> A.H.log2C;
+    // every CTA co-resident (cooperative launch), at most one per chunk
+    int64_t grid = std::min<int64_t>((int64_t)resident * sm_count(), n_chunks);
+    if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
+    grid = std::max<int64_t>(grid, 1);
+    StepArgs<T> a = A;
+    int np = n_p, sc = slots_cap;
+    void *args[] = {&a, &va, &vb, &np, &sc};
+    CFD_CUDA(cudaLaunchCooperativeKernel((void *)kern, dim3((unsigned)grid), dim3(STEP_WARPS * 32), args, smem, stream));
+    CFD_COUNT_LAUNCH();
+    return CFD_OK;
+}
+
+template <typename T, int NB, int VPT>
+cfd_status launch_persistent_staged_ch(const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, int n_p, int grid_cap,
+                                       cudaStream_t s) {
+    const bool fixed = A.H.log2C == 5 &&
+                       (uint64_t)A.H.n_rows * (uint64_t)((NB * (int64_t)sizeof(cplx_t<T>)) >> 4) < (1ULL << 32);
+    if (fixed) return launch_persistent_staged_nb<T, NB, VPT, 32>(A, va, vb, n_p, grid_cap, s);
+    return launch_persistent_staged_nb<T, NB, VPT, 0>(A, va, vb, n_p, grid_cap, s);
+}
+
+}  // namespace
+
+// General steps 3..n_p in one cooperative launch (packed values prepared in
+// A.prep_val; steps 1 and 2 already run).
+template <typename T>
+cfd_status launch_persistent_staged(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, int n_p,
+                                    int grid_cap, cudaStream_t s) {
+    if (!A.H.packed) return fail(CFD_ERR_ARG, "the staged persistent filter needs packed matrix values");
+    if (!A.status || !A.prep_val) return fail(CFD_ERR_INTERNAL, "staged persistent steps without status or values");
+#define CFD_PSCASE(NB_, VPT_) \
+    if (nb == NB_ && vpt == VPT_) return launch_persistent_staged_ch<T, NB_, VPT_>(A, va, vb, n_p, grid_cap, s);
+    CFD_PSCASE(8, 1)
+    CFD_PSCASE(8, 2)
+    CFD_PSCASE(16, 1)
+    CFD_PSCASE(16, 2)
+    CFD_PSCASE(32, 1)
+    CFD_PSCASE(32, 2)
+    CFD_PSCASE(64, 2)
+#undef CFD_PSCASE
+    return fail(CFD_ERR_ARG, "unsupported block width n_b=%d with %d vectors per thread", nb, vpt);
+}
 
 template <typename T, bool PACK>
 cfd_status launch_persistent_p(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, cplx_t<T> *xb,
