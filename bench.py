@@ -117,13 +117,18 @@ def parse():
                          "pipes; kernel: filter calls on one n_b block of the 64x64x32 lattice (profiling case)")
     ap.add_argument("--host-lattice", default="64x64x32", help="host mode: lattice Nx x Ny x Nz")
     ap.add_argument("--host-n-s", type=int, default=128, help="host mode: search space width")
+    ap.add_argument("--host-n-ps", default="2,5,10,20,50,100", help="host mode: filter degrees (comma list)")
     ap.add_argument("--realisations", type=int, default=workloads.BATCH_COUNT)
     ap.add_argument("--prec", default="c128", choices=["c128", "c64"], help="filter arithmetic")
-    ap.add_argument("--gather", type=int, default=0,
-                    help="kernel mode: cfd_filter_opts.gather (double-word step: 16 loads X before the gathers)")
-    ap.add_argument("--arith", default="native", choices=["native", "dw"],
-                    help="complex128 filter: native fp64 arithmetic or double-word arithmetic on the fp32 pipe "
-                         "for the general steps (cfd_filter_opts.arith = 1)")
+    ap.add_argument("--gather", type=int, default=0, help="kernel mode: cfd_filter_opts.gather")
+    ap.add_argument("--vpt", type=int, default=0, help="kernel mode: vectors per thread (0: default)")
+    ap.add_argument("--no-moments", action="store_true", help="kernel mode: filter without moments")
+    ap.add_argument("--arith", default="dw", choices=["native", "dw"],
+                    help="complex128 filter: double-word arithmetic on the fp32 pipe (cfd_filter_opts.arith = 1, "
+                         "the default) or native fp64 arithmetic")
+    ap.add_argument("--tte-policies", default="fp64,mixed_dw",
+                    help="time to eigenpairs: comma list of fp64, fp64_dw, mixed, mixed_dw (the first is the "
+                         "reference the others' speedups and eigenvalue differences are taken against)")
     ap.add_argument("--storage", default="packed", choices=["packed", "complex"],
                     help="matrix values as real-or-imaginary scalars (exact for Topi) or complex pairs")
     a = ap.parse_args()
@@ -384,20 +389,27 @@ def run_filter(a):
     b.cfd_workspace_status(work)         # a recorded device-side error voids the run
 
     # per-launch time of the general fused step: a step's time less that of
-    # the same call with n_p = 2 (weights, prepared values, steps 1 and 2,
-    # moments), over its n_p - 2 general steps; CUDA events on the launch stream
+    # the same call with n_p = 3 (weights, prepared values, steps 1 and 2, one
+    # general step, moments), over its n_p - 3 remaining general steps; CUDA
+    # events on the launch stream
     t_steps = sorted(ev[k].elapsed_time(ev[k + 1]) / 1e3 for k in range(a.steps))
     t_med = t_steps[len(t_steps) // 2]
-    cal = []
-    for k in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        filt(blocks[k % n_blocks], 2)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        cal.append(e0.elapsed_time(e1) / 1e3)
-    t_fixed = sorted(cal)[1]
-    t_launch = (t_med - t_fixed) / (n_p - 2)
+
+    mu3 = torch.empty(n_b, 6, dtype=torch.float64, device="cuda")
+
+    def fixed_part(o):
+        cal = []
+        for k in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b._check(L.cfd_filter_ex(H.ref(), lmin, lmax, lam_l, lam_r, 3, blocks[k % n_blocks], n_b, b._ptr(work),
+                                     work.numel(), b._ptr(mu3), b.ctypes.byref(o), b._stream()))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cal.append(e0.elapsed_time(e1) / 1e3)
+        return sorted(cal)[1]
+    t_fixed = fixed_part(opts)
+    t_launch = (t_med - t_fixed) / (n_p - 3)
 
     step_bytes = model.step_bytes(N, nnz, n_b, prec)
     value = world * a.steps * n_p * step_bytes / t / 1e9
@@ -436,8 +448,44 @@ def run_filter(a):
                 "peak_source": hbm_src, "kernel": "k_cheb_step_staged<float,%d,2,moments,%s>" % (n_b, a.storage),
                 "algorithmic": "nnz (8 + 4) + 5 N n_b 8 bytes per launch",
                 "avg_launch_ms": round(1e3 * t_launch, 4)}
-    roof["avg_launch_note"] = ("(median step - median n_p=2 call) / (n_p - 2), CUDA events on the launch stream; "
-                               "fixed part %.2f ms" % (1e3 * t_fixed))
+    roof["avg_launch_note"] = ("(median step - median n_p=3 call) / (n_p - 3), CUDA events on the launch stream; "
+                               "n_p=3 call %.2f ms" % (1e3 * t_fixed))
+
+    native = None
+    if dw:
+        # the same block step with the native fp64 arithmetic, and the
+        # double-word result's distance from it (filtered block, moments)
+        onat = b.cfd_filter_opts(0, 0, 0, 0, 0, 0, 0, 0)
+        X0 = X[:, :n_b].contiguous()
+        Xd, Xn = X0.clone(), X0.clone()
+        mu_n = torch.empty_like(mu)
+        bn = b.block_of(Xn)
+        tn = []
+        for k in range(3):
+            Xn.copy_(X0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b._check(L.cfd_filter_ex(H.ref(), lmin, lmax, lam_l, lam_r, n_p, bn, n_b, b._ptr(work), work.numel(),
+                                     b._ptr(mu_n), b.ctypes.byref(onat), b._stream()))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k:
+                tn.append(e0.elapsed_time(e1) / 1e3)
+        filt(b.block_of(Xd))
+        torch.cuda.synchronize()
+        err_x = float(torch.linalg.norm(Xd - Xn) / torch.linalg.norm(Xn))
+        err_mu = float(torch.max(torch.abs(mu - mu_n)) / torch.max(torch.abs(mu_n)))
+        nominal, measured = fp64_peak(b)
+        t_nat = statistics.median(tn)
+        fma = model.step_fma_flops(N, nnz, n_b, packed=(a.storage == "packed"), prepared=True)
+        tl_nat = (t_nat - fixed_part(onat)) / (n_p - 3)
+        native = {"ms_per_step": round(1e3 * t_nat, 3), "gbs": round(n_p * step_bytes / t_nat / 1e9, 1),
+                  "avg_launch_ms": round(1e3 * tl_nat, 4),
+                  "fp64_pipe_gflops": round(fma / tl_nat / 1e9, 1), "fp64_peak_gflops": round(nominal, 1),
+                  "fp64_peak_measured_gflops": round(measured, 1) if measured else None,
+                  "speedup_dw": round(t_nat / t_med, 3),
+                  "dw_vs_native_rel_frobenius": err_x, "dw_vs_native_moments_rel": err_mu}
+        del X0, Xd, Xn
 
     e2e = None
     if not a.no_e2e:
@@ -473,7 +521,7 @@ def run_filter(a):
     if not a.no_tte and rank == 0:
         tw = workloads.ALL[a.tte_workload] if a.tte_workload else TTE_WORKLOAD
         tp, tH, tlmin, tlmax, tl, tr, kpm = setup_problem(b, tw, tw.seed, a.storage, with_kpm=True)
-        tte = time_to_eigenpairs(b, tw, tp, tH, tlmin, tlmax, tl, tr, a.storage)
+        tte = time_to_eigenpairs(b, tw, tp, tH, tlmin, tlmax, tl, tr, a.storage, tuple(a.tte_policies.split(",")))
         tte["workload"] = tw.name
         tte["kpm_count_in_window"] = round(kpm, 2)
         del tH
@@ -502,6 +550,8 @@ def run_filter(a):
                           "parallelism": "replicas" if world > 1 else "single"},
                "gflops": round(gflops, 2), "roofline": roof, "clocks": clocks, "gpu_launches": launches,
                "cpu_baseline": cpu, "e2e": e2e}
+        if native is not None:
+            out["native_fp64"] = native
         if tte is not None:
             out["time_to_eigenpairs"] = tte
         print(json.dumps(out))
@@ -624,7 +674,8 @@ def run_iteration(a):
         e2e = {"value": round(world * a.steps * filt_bytes / te / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + n_s * 8}
 
-    tte = time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a.storage) if (a.tte and rank == 0) else None
+    tte = time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a.storage,
+                             tuple(a.tte_policies.split(","))) if (a.tte and rank == 0) else None
 
     if rank == 0:
         cpu = None
@@ -659,17 +710,26 @@ def run_iteration(a):
         dist.destroy_process_group()
 
 
-def time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, storage):
+POLICIES = {"fp64": ("CFD_POLICY_FP64", False), "fp64_dw": ("CFD_POLICY_FP64_DW", False),
+            "mixed": ("CFD_POLICY_MIXED", True), "mixed_dw": ("CFD_POLICY_MIXED_DW", True)}
+
+
+def time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, storage, policies=("fp64", "mixed_dw")):
     """Wall time of cfd_solve to n_t eigenpairs at residual <= 1e-10 from a random
-    start block, fp64 policy vs mixed policy (fp32 filter, then fp64), with
-    the workload's n_p and n_b."""
+    start block for each policy (fp64: native fp64 filter; fp64_dw: double-word
+    filter; mixed: fp32 filter, then fp64; mixed_dw: fp32 filter, then
+    double-word), with the workload's n_p and n_b.  The first policy is the
+    reference of the speedups and eigenvalue differences."""
     import numpy as np
     import torch
     suffix = "p" if storage == "packed" else ""
-    Hl = b.cfd_build_matrix(p, w.sell_C, w.sell_sigma, "c64" + suffix)
+    Hl = b.cfd_build_matrix(p, w.sell_C, w.sell_sigma, "c64" + suffix) if any(
+        POLICIES[q][1] for q in policies) else None
     out = {}
     res = {}
-    for name, pol, hl in (("fp64", b.CFD_POLICY_FP64, None), ("mixed", b.CFD_POLICY_MIXED, Hl)):
+    for name in policies:
+        pol = getattr(b, POLICIES[name][0])
+        hl = Hl if POLICIES[name][1] else None
         X = torch.empty(H.N, w.n_s, dtype=torch.complex128, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -686,18 +746,21 @@ def time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, storage):
         del X
         torch.cuda.empty_cache()
     # each run may converge a pair or two the other has not reached yet (the
-    # levels come in degenerate pairs): match every fp64 eigenvalue with the
-    # nearest mixed one and compare the pairs both runs found
-    a, m = res["fp64"], res["mixed"]
-    if len(a) and len(m):
-        d = np.abs(a[:, None] - m[None, :]).min(axis=1)
-        both = d < 1e-8
-        out["common_pairs"] = int(both.sum())
-        out["max_eval_diff_mixed_vs_fp64"] = float(d[both].max()) if both.any() else None
-    else:
-        out["common_pairs"] = 0
-        out["max_eval_diff_mixed_vs_fp64"] = None
-    out["speedup_mixed"] = round(out["fp64"]["seconds"] / out["mixed"]["seconds"], 3)
+    # levels come in degenerate pairs): match every reference eigenvalue with
+    # the nearest one of the other run and compare the pairs both found
+    ref = policies[0]
+    for name in policies[1:]:
+        a, m = res[ref], res[name]
+        if len(a) and len(m):
+            d = np.abs(a[:, None] - m[None, :]).min(axis=1)
+            both = d < 1e-8
+            out[name]["common_pairs"] = int(both.sum())
+            out[name]["max_eval_diff_vs_" + ref] = float(d[both].max()) if both.any() else None
+        else:
+            out[name]["common_pairs"] = 0
+            out[name]["max_eval_diff_vs_" + ref] = None
+        out[name]["speedup_vs_" + ref] = round(out[ref]["seconds"] / out[name]["seconds"], 3)
+    out["reference_policy"] = ref
     out["tol"] = 1e-10
     out["n_t"] = w.n_t
     out["n_s"] = w.n_s
@@ -880,59 +943,86 @@ def run_fusion(a):
 
 def run_host(a):
     """Search space in host memory (Sect. 5's larger-than-fast-memory case):
-    the filter with X resident in HBM (cfd_filter) against X in page-locked
+    the filter with X resident in HBM (cfd_filter_ex) against X in page-locked
     host memory streamed block by block over the chip-to-chip link
-    (cfd_filter_host), complex128 packed, for several n_p.  The host penalty
-    is (t_host - t_device) / t_device."""
+    (cfd_filter_host_ex), complex128 packed, --arith, for several n_p.  The
+    host penalty is (t_host - t_device) / t_device.  The start block is drawn
+    on the device (seeded) and copied into one page-locked host buffer; both
+    are refilled from the seed before every run, so no second copy of X is
+    held anywhere (the N x 512 block of the 200x200x100 lattice is 131 GB)."""
     import torch
     from paper_1803_02156_gb300 import binding as b, inputs
     torch.cuda.set_device(0)
     w = WORKLOAD
     L = tuple(int(v) for v in a.host_lattice.split("x"))
     n_s, n_b = a.host_n_s, a.n_b
+    arith = 1 if a.arith == "dw" else 0
     p = b.topi_params(*L, t=w.t, m=w.m, gamma=w.gamma, seed=w.seed, periodic=w.periodic)
     H = b.cfd_build_matrix(p, w.sell_C, w.sell_sigma, "c128p")
     N, nnz = H.N, H.nnz
-    Xh = torch.from_numpy(inputs.gaussian_block(N, n_s, seed=w.x_seed)).pin_memory()
-    X0 = Xh.clone()
-    n_ps = [2, 5, 10, 20, 50, 100]
+    n_ps = [int(v) for v in a.host_n_ps.split(",")]
     ws = max(b.cfd_filter_host_workspace(N, n_s, n_b, max(n_ps), "c128", "c128"),
              b.cfd_filter_workspace(N, n_s, n_b, max(n_ps), "c128", "c128"))
     work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    dev = torch.empty(N, n_s, dtype=torch.complex128, device="cuda")
+    # page-locked by registering exactly the array's bytes (torch's pinned
+    # allocator would round a 131 GB request up to a power of two)
+    import numpy as np
+    Xn = np.empty((N, n_s), dtype=np.complex128)
+    rc = torch.cuda.cudart().cudaHostRegister(Xn.ctypes.data, Xn.nbytes, 0)
+    if int(rc) != 0:
+        raise RuntimeError("cudaHostRegister of %d bytes failed (%s)" % (Xn.nbytes, rc))
+    Xh = torch.from_numpy(Xn)
     stream = torch.cuda.current_stream()
+    o = b.cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0)
+
+    def reset():
+        inputs.fill_gaussian_device(dev, w.x_seed)
+        Xh.copy_(dev)
+        torch.cuda.synchronize()
+
+    def timed(f):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        f()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
     rows = []
     for n_p in n_ps:
-        dev = torch.empty(N, n_s, dtype=torch.complex128, device="cuda")
-
         def run_dev():
-            b.cfd_filter(H, *BOUNDS, -0.3, 0.3, n_p, dev, n_b, work=work)
+            b._check(b.lib().cfd_filter_ex(H.ref(), BOUNDS[0], BOUNDS[1], -0.3, 0.3, n_p, b.block_of(dev), n_b,
+                                           b._ptr(work), work.numel(), b._ptr(None), b.ctypes.byref(o),
+                                           b._stream(stream)))
 
         def run_host_():
-            b._check(b.lib().cfd_filter_host(H.ref(), BOUNDS[0], BOUNDS[1], -0.3, 0.3, n_p, b.block_of(Xh), n_b,
-                                             b._ptr(work), work.numel(), b._ptr(None), b._stream(stream)))
-        res = {}
-        for name, f, reset in (("device", run_dev, lambda: dev.copy_(X0, non_blocking=True)),
-                               ("host", run_host_, lambda: Xh.copy_(X0))):
-            ts = []
-            for r in range(a.warmup + a.steps):
-                reset()
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                f()
-                e1.record()
-                torch.cuda.synchronize()
-                if r >= a.warmup:
-                    ts.append(e0.elapsed_time(e1) / 1e3)
-            res[name] = statistics.median(ts)
+            b._check(b.lib().cfd_filter_host_ex(H.ref(), BOUNDS[0], BOUNDS[1], -0.3, 0.3, n_p, b.block_of(Xh), n_b,
+                                                b._ptr(work), work.numel(), b._ptr(None), b.ctypes.byref(o),
+                                                b._stream(stream)))
+        res = {"device": [], "host": []}
+        for r in range(a.warmup + a.steps):
+            reset()
+            td = timed(run_dev)
+            th = timed(run_host_)
+            if r >= a.warmup:
+                res["device"].append(td)
+                res["host"].append(th)
+        # the host filter's result equals the device filter's (sampled rows)
+        idx = torch.linspace(0, N - 1, 4096, dtype=torch.int64)
+        same = bool(torch.equal(Xh[idx], dev[idx.cuda()].cpu()))
+        td, th = statistics.median(res["device"]), statistics.median(res["host"])
         moved = 2 * N * n_s * 16
-        rows.append({"n_p": n_p, "device_s": round(res["device"], 5), "host_s": round(res["host"], 5),
-                     "penalty": round(res["host"] / res["device"] - 1.0, 4),
-                     "host_link_gbs_if_serial": round(moved / max(res["host"] - res["device"], 1e-9) / 1e9, 1),
-                     "filter_gbs_host": round(model.filter_bytes(N, nnz, n_s, n_b, n_p) / res["host"] / 1e9, 1)})
-        del dev
+        rows.append({"n_p": n_p, "device_s": round(td, 5), "host_s": round(th, 5),
+                     "penalty": round(th / td - 1.0, 4), "link_gbs_if_serial": round(moved / max(th - td, 1e-9) / 1e9, 1),
+                     "filter_gbs_device": round(model.filter_bytes(N, nnz, n_s, n_b, n_p) / td / 1e9, 1),
+                     "filter_gbs_host": round(model.filter_bytes(N, nnz, n_s, n_b, n_p) / th / 1e9, 1),
+                     "host_equals_device": same})
+    torch.cuda.cudart().cudaHostUnregister(Xn.ctypes.data)
     print(json.dumps({"metric": "filter time, search space in host memory vs HBM", "unit": "s", "n_gpus": 1,
                       "steps": a.steps, "warmup": a.warmup, "data": "synthetic", "dtype": "c128",
+                      "arith": a.arith,
                       "config": {"workload": "topi-%s" % a.host_lattice, "N": N, "n_s": n_s, "n_b": n_b,
                                  "host_bytes": N * n_s * 16, "storage": "packed", "pinned": True},
                       "results": rows}))
@@ -1010,7 +1100,7 @@ def run_tte(a):
     torch.cuda.set_device(0)
     w = workloads.ALL[a.tte_workload] if a.tte_workload else TTE_WORKLOAD
     p, H, lmin, lmax, lam_l, lam_r, kpm = setup_problem(b, w, w.seed, a.storage, with_kpm=True)
-    res = time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a.storage)
+    res = time_to_eigenpairs(b, w, p, H, lmin, lmax, lam_l, lam_r, a.storage, tuple(a.tte_policies.split(",")))
     res["kpm_count_in_window"] = round(kpm, 2)
     print(json.dumps({"metric": "time to eigenpairs, fp64 vs mixed", "unit": "s", "n_gpus": 1, "data": "synthetic",
                       "higher_is_better": False,
@@ -1037,14 +1127,16 @@ def run_kernel(a):
     for r in range(a.warmup + a.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        b.cfd_filter_ex(H, *BOUNDS, -0.3, 0.3, a.n_p, X, a.n_b, moments=True, arith=1 if dw else 0, gather=a.gather)
+        b.cfd_filter_ex(H, *BOUNDS, -0.3, 0.3, a.n_p, X, a.n_b, moments=not a.no_moments, arith=1 if dw else 0,
+                        gather=a.gather, vpt=a.vpt)
         e1.record()
         torch.cuda.synchronize()
         if r >= a.warmup:
             ts.append(e0.elapsed_time(e1) / 1e3)
     t = statistics.median(ts) / a.n_p
     print(json.dumps({"metric": "filter call, ms per step", "unit": "ms", "workload": w.name, "prec": prec,
-                      "arith": "dw" if dw else "native", "gather": a.gather, "n_b": a.n_b, "n_p": a.n_p,
+                      "arith": "dw" if dw else "native", "gather": a.gather, "vpt": a.vpt,
+                      "moments": not a.no_moments, "n_b": a.n_b, "n_p": a.n_p,
                       "ms_per_step": round(1e3 * t, 4),
                       "model_gbs": round(model.step_bytes(H.N, H.nnz, a.n_b, prec) / t / 1e9, 1)}))
 

@@ -338,6 +338,13 @@ cfd_status cfd_filter_host(const cfd_matrix *H, double lmin, double lmax, double
                            int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
                            double *moments, cudaStream_t stream);
 
+/* cfd_filter_host with the arithmetic option of cfd_filter_opts (arith; every
+ * other field must be zero): arith = 1 runs the complex-double steps in
+ * double-word arithmetic, as cfd_filter_ex does. */
+cfd_status cfd_filter_host_ex(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                              int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,
+                              const cfd_filter_opts *opts, cudaStream_t stream);
+
 /*
  * Chebyshev moments only (the kernel polynomial method: Algorithm 1 without
  * line 12, Sect. 2): for the columns of R (N x n_s, the matrix's precision,

@@ -124,6 +124,10 @@ _PROTOS = {
     "cfd_filter_host": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "cfd_filter_host_ex": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                          ctypes.POINTER(cfd_filter_opts), ctypes.c_void_p]),
     "cfd_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cfd_kpm_moments": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        cfd_block, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
@@ -382,10 +386,11 @@ def cfd_filter_host_workspace(N, n_s, n_b, n_p, prec_H, prec_X):
 
 
 def cfd_filter_host(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=None, stream=None,
-                    device="cuda"):
+                    device="cuda", arith=0):
     """cfd_filter for X in host memory (a CPU tensor, pinned for overlap); X is
     filtered in place once the stream is synchronised (this call synchronises
-    it).  Returns the device moments when moments=True."""
+    it).  Returns the device moments when moments=True.  arith 1: double-word
+    complex-double steps (cfd_filter_host_ex)."""
     if X.is_cuda:
         raise ValueError("cfd_filter_host takes a host (CPU) tensor")
     blk = block_of(X)
@@ -393,8 +398,9 @@ def cfd_filter_host(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, wor
     if work is None or work.numel() < ws:
         work = _workspace(ws, device)
     mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=device) if moments else None
-    _check(lib().cfd_filter_host(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
-                                 _ptr(mu), _stream(stream)))
+    o = cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0)
+    _check(lib().cfd_filter_host_ex(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
+                                    _ptr(mu), ctypes.byref(o), _stream(stream)))
     (stream or torch.cuda.current_stream()).synchronize()
     return mu
 

@@ -354,21 +354,24 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
             A.dots = nullptr;
             CFD_TRY(launch_persistent<T>(n_b, vpt, A, va, vb, xb, ldx, n_p, P.grid_cap, stream));
         } else {
+            // double-word steps (n_p >= 3): X_b to double-word form first; the
+            // last general step writes it back as complex double
+            const bool dws = dw && n_p >= 3;
+            if (dws) CFD_TRY(launch_dw_convert(xb, ldx, X.n_rows, n_b, true, stream));
             // step 1: V1 = H~ X_b
             A.vin = xb; A.ldin = ldx; A.w = va; A.ldw = n_b; A.x = nullptr; A.ldx = 0;
             A.a = P.alpha; A.p = 1; A.dots = moments ? ws.raw : nullptr;
-            CFD_TRY(launch_step<T>(STEP_FIRST, n_b, vpt, A, P.grid_cap, stream));
+            if constexpr (std::is_same<T, double>::value) {
+                if (dws) CFD_TRY(launch_step_dw(STEP_FIRST, n_b, vpt, A, false, P.grid_cap, stream));
+            }
+            if (!dws) CFD_TRY(launch_step<T>(STEP_FIRST, n_b, vpt, A, P.grid_cap, stream));
             // step 2: V2 = 2 H~ V1 - X_b, X_b = gc0 X_b + gc1 V1 + gc2 V2
             A.vin = va; A.ldin = n_b; A.w = vb; A.ldw = n_b; A.x = xb; A.ldx = ldx;
             A.a = 2.0 * P.alpha; A.p = 2; A.dots = moments ? ws.raw + 2 * n_b : nullptr;
-            CFD_TRY(launch_step<T>(STEP_SECOND, n_b, vpt, A, P.grid_cap, stream));
-            if (dw && n_p >= 3) {
-                // the recurrence blocks and X_b to double-word form; the last
-                // general step writes X_b back as complex double
-                CFD_TRY(launch_dw_convert(va, n_b, X.n_rows, n_b, true, stream));
-                CFD_TRY(launch_dw_convert(vb, n_b, X.n_rows, n_b, true, stream));
-                CFD_TRY(launch_dw_convert(xb, ldx, X.n_rows, n_b, true, stream));
+            if constexpr (std::is_same<T, double>::value) {
+                if (dws) CFD_TRY(launch_step_dw(STEP_SECOND, n_b, vpt, A, false, P.grid_cap, stream));
             }
+            if (!dws) CFD_TRY(launch_step<T>(STEP_SECOND, n_b, vpt, A, P.grid_cap, stream));
             // steps 3..n_p: swap(V_prev, V_cur); V_prev = 2 H~ V_cur - V_prev; X_b += gc_p V_prev
             for (int p = 3; p <= n_p; ++p) {
                 C *cur = (p & 1) ? vb : va;
@@ -377,7 +380,7 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
                 A.dots = moments ? ws.raw + (int64_t)(p - 1) * 2 * n_b : nullptr;
                 if constexpr (std::is_same<T, double>::value) {
                     if (dw) {
-                        CFD_TRY(launch_step_dw(n_b, vpt, A, p == n_p, P.grid_cap, stream));
+                        CFD_TRY(launch_step_dw(STEP_GENERAL, n_b, vpt, A, p == n_p, P.grid_cap, stream));
                         continue;
                     }
                 }

@@ -20,6 +20,34 @@ enum StepKind : int {
     STEP_GENERAL = 2   // w = a (H vin - beta vin) - w; x += g_p w            (lines 9-12)
 };
 
+// Order in which the CTAs of a staged step take the SELL chunks: 0 grid-stride
+// (CTA b takes chunks b, b + grid, ...: at any time the GPU works on one
+// window of rows); 1 contiguous ranges (CTA b takes ceil(n / grid)
+// consecutive chunks, so a row's y-neighbours, a few chunks back, were
+// gathered by the same CTA moments before and may still sit in its L1).
+#ifndef CFD_STAGED_RASTER
+#define CFD_STAGED_RASTER 0
+#endif
+
+struct ChunkRange {
+    int64_t first, last, stride;
+};
+
+__device__ __forceinline__ ChunkRange cta_chunks(int64_t n_chunks) {
+    ChunkRange r;
+    if (CFD_STAGED_RASTER) {
+        const int64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
+        r.first = (int64_t)blockIdx.x * per;
+        r.last = r.first + per < n_chunks ? r.first + per : n_chunks;
+        r.stride = 1;
+    } else {
+        r.first = blockIdx.x;
+        r.last = n_chunks;
+        r.stride = gridDim.x;
+    }
+    return r;
+}
+
 // Arguments of one step launch.  Row i of an operand sits at ptr + i * ld.
 // dots receives, per vector j, (<vin_j, vin_j>, Re <w_j, vin_j>).
 template <typename T>
@@ -82,11 +110,12 @@ template <typename T>
 cfd_status launch_persistent_staged(int nb, int vpt, const StepArgs<T> &A, cplx_t<T> *va, cplx_t<T> *vb, int n_p,
                                     int grid_cap, cudaStream_t s);
 
-// Complex-double general steps in double-word arithmetic on the fp32 pipe
-// (step_dw.cu): the step for general step p (last: X written back as
-// complex double), the in-place conversion of a block between complex double
-// and double-word form, and the double-word prepared values.
-cfd_status launch_step_dw(int nb, int vpt, const StepArgs<double> &A, bool last, int grid_cap, cudaStream_t s);
+// Complex-double steps in double-word arithmetic on the fp32 pipe
+// (step_dw.cu): step 1, 2 or a general step (last: X written back as complex
+// double), the in-place conversion of a block between complex double and
+// double-word form, and the double-word prepared values.
+cfd_status launch_step_dw(int kind, int nb, int vpt, const StepArgs<double> &A, bool last, int grid_cap,
+                          cudaStream_t s);
 cfd_status launch_dw_convert(void *p, int64_t ld, int64_t n_rows, int nb, bool to_dw, cudaStream_t stream);
 cfd_status launch_prepare_values_dw(const cfd_matrix *H, double alpha, double beta, const int32_t *chunk_rid,
                                     const double *rcoef, int64_t rcoef_ld, void *out, size_t out_bytes,

@@ -51,10 +51,9 @@ extern "C" size_t cfd_filter_host_workspace(int64_t N, int n_s, int n_b, int n_p
     return host_filter_workspace(N, n_b, n_p, prec_H & 0xff, prec_X & 0xff);
 }
 
-extern "C" cfd_status cfd_filter_host(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
-                                      int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,
-                                      cudaStream_t stream) {
-    clear_error();
+static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                                   int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,
+                                   int arith, cudaStream_t stream) {
     CFD_TRY(check_matrix(H));
     CFD_TRY(validate_block(X, H->n_rows));
     if (n_b != 8 && n_b != 16 && n_b != 32 && n_b != 64) return fail(CFD_ERR_ARG, "n_b=%d not in {8,16,32,64}", n_b);
@@ -97,8 +96,8 @@ extern "C" cfd_status cfd_filter_host(const cfd_matrix *H, double lmin, double l
         D.ptr = dbuf[b & 1];
         D.ld = n_b;
         D.n_cols = n_b;
-        CFD_TRY(filter_impl(H, lmin, lmax, lam_l, lam_r, n_p, D, n_b, 0, 0, work, fws,
-                            moments ? moments + (int64_t)b * n_b * 2 * n_p : nullptr, stream));
+        CFD_TRY(filter_impl_opts(H, lmin, lmax, lam_l, lam_r, n_p, D, n_b, 0, 0, 0, 0, work, fws,
+                                 moments ? moments + (int64_t)b * n_b * 2 * n_p : nullptr, stream, 0, 0, arith));
         CFD_CUDA(cudaEventRecord(cp.done[b & 1], stream));
         // write block b back, then reuse its buffer for block b + 2
         CFD_CUDA(cudaStreamWaitEvent(cp.copy, cp.done[b & 1], 0));
@@ -110,4 +109,23 @@ extern "C" cfd_status cfd_filter_host(const cfd_matrix *H, double lmin, double l
     CFD_CUDA(cudaEventRecord(cp.out, cp.copy));
     CFD_CUDA(cudaStreamWaitEvent(stream, cp.out, 0));
     return CFD_OK;
+}
+
+extern "C" cfd_status cfd_filter_host(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                                      int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,
+                                      cudaStream_t stream) {
+    clear_error();
+    return filter_host_impl(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, work, work_bytes, moments, ARITH_NATIVE,
+                            stream);
+}
+
+extern "C" cfd_status cfd_filter_host_ex(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                                         int n_p, cfd_block X, int n_b, void *work, size_t work_bytes,
+                                         double *moments, const cfd_filter_opts *opts, cudaStream_t stream) {
+    clear_error();
+    if (opts && (opts->vpt || opts->grid_cap || opts->persistent || opts->staged || opts->gather ||
+                 opts->fixed_chunk || opts->graph))
+        return fail(CFD_ERR_ARG, "cfd_filter_host_ex takes only the arith option");
+    return filter_host_impl(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, work, work_bytes, moments,
+                            opts ? opts->arith : ARITH_NATIVE, stream);
 }

@@ -1,5 +1,5 @@
-// General fused ChebFD step (Algorithm 1, lines 9-12) for complex double data
-// in double-word arithmetic on the fp32 pipe.
+// Fused ChebFD steps (Algorithm 1) for complex double data in double-word
+// arithmetic on the fp32 pipe.
 //
 // GB300 executes fp64 fused multiply-adds at 1/64 of the fp32 rate, so the
 // native complex128 step is bound by the FP64 pipe at about a fifth of the
@@ -21,7 +21,7 @@
 // Storage stays 16 bytes per complex element: the recurrence blocks V_a, V_b
 // and, during one filter application, the caller's X block hold the
 // double-word form {re_hi, im_hi, re_lo, im_lo}; the driver converts X to it
-// after step 2 and back to complex double after the last step.  The matrix
+// before step 1 and the last step writes it back as complex double.  The matrix
 // values are prepared once per application as the double-word form of
 // 2 alpha (H - beta) (8 bytes per packed slot, the bytes of a packed double),
 // so the minimum traffic per step equals the native step's.
@@ -68,14 +68,33 @@ __device__ __forceinline__ float4 ld_nc4(const float4 *p) { return __ldg(p); }
 
 }  // namespace
 
-// Arguments: those of the native general step (StepArgs<double>); the block
-// pointers hold double-words, prep_val the double-word prepared values
-// (float2 {hi, lo} per slot).  LAST: X is written back as complex double.
-// EARLY: a row's X and own V_cur entries are loaded before its gathers (their
-// latency overlaps the row sum, registers held across it: two CTAs per SM);
-// else after the row sum (three CTAs per SM).
-template <int NB, int VPT, bool MOM, int CH, bool LAST, bool EARLY>
-__global__ void __launch_bounds__(STEP_WARPS * 32, EARLY ? 2 : 3)
+// Gathers of a row in flight together (group size) and the CTAs per SM the
+// registers are capped for: the tuned values; both fixed at compile time.
+#ifndef CFD_DW_GROUP
+#define CFD_DW_GROUP 2
+#endif
+#ifndef CFD_DW_MIN_CTAS
+#define CFD_DW_MIN_CTAS 4
+#endif
+
+// x h for a double-word x and a float h that is a power of two (exact).
+__device__ __forceinline__ float4 dw_scale(float4 v, float h) {
+    return make_float4(v.x * h, v.y * h, v.z * h, v.w * h);
+}
+
+// One fused step (KIND: STEP_FIRST, STEP_SECOND or STEP_GENERAL, Algorithm 1
+// lines 4-6 and 9-12) with the prepared values P = 2 alpha (H - beta):
+//   first:   V1 = (1/2) P X                       (X: vin)
+//   second:  V2 = P V1 - X;  X <- g0 X + g1 V1 + g2 V2
+//   general: V_new = P V_cur - V_prev;  X <- X + g_p V_new
+// with the moments' dots <vin, vin>, Re <w, vin>.  Arguments: those of the
+// native steps (StepArgs<double>); the block pointers hold double-words,
+// prep_val the double-word prepared values (float2 {hi, lo} per slot).
+// LAST: X is written back as complex double.  A row's X and own vin entries
+// are loaded after its row sum (loading them before holds their registers
+// across the gathers and costs a resident CTA: measured slower).
+template <int NB, int VPT, int KIND, bool MOM, int CH, bool LAST>
+__global__ void __launch_bounds__(STEP_WARPS * 32, CFD_DW_MIN_CTAS)
 k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
     constexpr int TPR = NB / VPT;
     constexpr int RPW = 32 / TPR;
@@ -101,14 +120,20 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
     float4 *xdw = reinterpret_cast<float4 *>(A.x);
     const uint32_t tx_extra = A.staged == 2 ? 16u : 0u;
     const long long limit = A.staged == 2 ? (1LL << 24) : (1LL << 32);
-    // the step's weight g_p c_p as a double-word (in a batch: per chunk, that
-    // of the chunk's realisation)
-    float gh = 0.f, gl = 0.f;
-    auto set_weight = [&](double gd) {
-        gh = __double2float_rn(gd);
-        gl = __double2float_rn(gd - (double)gh);
+    // the step's weights as double-words: g_p c_p (general), g_0 c_0,
+    // g_1 c_1, g_2 c_2 (second); in a batch per chunk, those of its realisation
+    float gh[3] = {0.f, 0.f, 0.f}, gl[3] = {0.f, 0.f, 0.f};
+    constexpr int NW = KIND == STEP_SECOND ? 3 : (KIND == STEP_GENERAL ? 1 : 0);
+    auto set_weights = [&](const double *g) {
+#pragma unroll
+        for (int t = 0; t < NW; ++t) {
+            const double gd = g[t];
+            gh[t] = __double2float_rn(gd);
+            gl[t] = __double2float_rn(gd - (double)gh[t]);
+        }
     };
-    if (!A.chunk_rid) set_weight(A.gc[A.p]);
+    const int w0 = KIND == STEP_GENERAL ? A.p : 0;
+    if (!A.chunk_rid && NW) set_weights(A.gc + w0);
     // 32-bit gather offsets (16-byte units) when the chunk height is compiled in
     const uint32_t ld16 = (uint32_t)A.ldin;
     float uu_s[VPT], uu_e[VPT], wu_s[VPT], wu_e[VPT];
@@ -139,43 +164,36 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
     int k = 0;
     bool ok = true;
     bool prefetched = false;
-    if (tid == 0 && (int64_t)blockIdx.x < n_chunks) issue(blockIdx.x, 0);
+    const ChunkRange cr = cta_chunks(n_chunks);
+    if (tid == 0 && cr.first < cr.last) issue(cr.first, 0);
     __syncthreads();
-    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++k) {
+    for (int64_t c = cr.first; c < cr.last; c += cr.stride, ++k) {
         const int b = k & 1;
-        prefetched = c + gridDim.x < n_chunks;
-        if (tid == 0 && prefetched) issue(c + gridDim.x, b ^ 1);
+        prefetched = c + cr.stride < cr.last;
+        if (tid == 0 && prefetched) issue(c + cr.stride, b ^ 1);
         const bool landed = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);
         if (landed) {
             const int cl = s_len[b];
             const int nre = cl & 0xffff;
             const int len = nre + (cl >> 16);
-            if (A.chunk_rid) set_weight(__ldg(A.rcoef + (int64_t)__ldg(A.chunk_rid + c) * A.rcoef_ld + 2 + A.p));
+            if (A.chunk_rid && NW) set_weights(A.rcoef + (int64_t)__ldg(A.chunk_rid + c) * A.rcoef_ld + 2 + w0);
             for (int rr = warp * RPW + sub; rr < chunk_h; rr += STEP_WARPS * RPW) {
                 const int64_t r = (c << log2C) + rr;
                 if (r >= n_rows) continue;
                 const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
                 const int32_t *colp = col_s(b) + rr;
                 const float2 *valp = val_s(b) + rr;
-                // V_prev starts the row sum; the own row of V_cur (moments)
-                // and X are loaded here or after the sum (EARLY)
-                float4 u[VPT], wo[VPT], xo[VPT];
-                auto load_epilogue = [&]() {
-#pragma unroll
-                    for (int q = 0; q < VPT; ++q) {
-                        if (MOM) u[q] = ld_nc4(vin + i * A.ldin + j0 + q);
-                        xo[q] = xdw[i * A.ldx + j0 + q];
-                    }
-                };
-#pragma unroll
-                for (int q = 0; q < VPT; ++q) wo[q] = wout[i * A.ldw + j0 + q];
-                if (EARLY) load_epilogue();
-                // row sum started at -V_prev: (s, e) per real and imaginary part
+                // the row sum starts at -V_prev (general), -X (second) or 0:
+                // (s, e) per real and imaginary part
+                float4 u[VPT], xo[VPT];
                 float rs[VPT], re[VPT], is[VPT], ie[VPT];
 #pragma unroll
                 for (int q = 0; q < VPT; ++q) {
-                    rs[q] = -wo[q].x; re[q] = -wo[q].z;
-                    is[q] = -wo[q].y; ie[q] = -wo[q].w;
+                    float4 w0v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (KIND == STEP_GENERAL) w0v = wout[i * A.ldw + j0 + q];
+                    if (KIND == STEP_SECOND) w0v = xdw[i * A.ldx + j0 + q];
+                    rs[q] = -w0v.x; re[q] = -w0v.z;
+                    is[q] = -w0v.y; ie[q] = -w0v.w;
                 }
                 auto gather = [&](int kk, float4 (&v)[VPT]) {
                     const int cc = max(colp[kk << log2C], 0);          // padding: col -1, value 0
@@ -201,7 +219,7 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
                         }
                     }
                 };
-                constexpr int U = 4;
+                constexpr int U = CFD_DW_GROUP;
                 for (int g = 0; g < 2; ++g) {             // real group, then imaginary group
                     const bool imag = g == 1;
                     int kk = imag ? nre : 0;
@@ -219,22 +237,40 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
                         madd(kk, imag, v);
                     }
                 }
-                if (!EARLY) load_epilogue();
-                // V_new = the renormalised sum; X += g V_new; moments
+                // the own row of vin (moments; V1 in the second step's X
+                // update) and X
+#pragma unroll
+                for (int q = 0; q < VPT; ++q) {
+                    if (MOM || KIND == STEP_SECOND) u[q] = ld_nc4(vin + i * A.ldin + j0 + q);
+                    if (KIND != STEP_FIRST) xo[q] = xdw[i * A.ldx + j0 + q];
+                }
+                // the new vector = the renormalised sum; X update; moments
 #pragma unroll
                 for (int q = 0; q < VPT; ++q) {
                     float4 wn;
                     two_sum(rs[q], re[q], wn.x, wn.z);
                     two_sum(is[q], ie[q], wn.y, wn.w);
+                    if (KIND == STEP_FIRST) wn = dw_scale(wn, 0.5f);
                     wout[i * A.ldw + j0 + q] = wn;
-                    float xrh = xo[q].x, xrl = xo[q].z, xih = xo[q].y, xil = xo[q].w;
-                    dw_axpy(xrh, xrl, gh, gl, wn.x, wn.z);
-                    dw_axpy(xih, xil, gh, gl, wn.y, wn.w);
-                    if (LAST) {
-                        double2 *xd = reinterpret_cast<double2 *>(xdw + i * A.ldx + j0 + q);
-                        *xd = make_double2((double)xrh + (double)xrl, (double)xih + (double)xil);
-                    } else {
-                        xdw[i * A.ldx + j0 + q] = make_float4(xrh, xih, xrl, xil);
+                    if (KIND != STEP_FIRST) {
+                        float xrh = xo[q].x, xrl = xo[q].z, xih = xo[q].y, xil = xo[q].w;
+                        if (KIND == STEP_SECOND) {
+                            // g0 X + g1 V1 + g2 V2 as (0 + g0 X) + g1 V1 + g2 V2
+                            float ar = 0.f, al = 0.f, bi = 0.f, bl = 0.f;
+                            dw_axpy(ar, al, gh[0], gl[0], xrh, xrl);
+                            dw_axpy(bi, bl, gh[0], gl[0], xih, xil);
+                            dw_axpy(ar, al, gh[1], gl[1], u[q].x, u[q].z);
+                            dw_axpy(bi, bl, gh[1], gl[1], u[q].y, u[q].w);
+                            xrh = ar; xrl = al; xih = bi; xil = bl;
+                        }
+                        dw_axpy(xrh, xrl, gh[NW - 1], gl[NW - 1], wn.x, wn.z);
+                        dw_axpy(xih, xil, gh[NW - 1], gl[NW - 1], wn.y, wn.w);
+                        if (LAST) {
+                            double2 *xd = reinterpret_cast<double2 *>(xdw + i * A.ldx + j0 + q);
+                            *xd = make_double2((double)xrh + (double)xrl, (double)xih + (double)xil);
+                        } else {
+                            xdw[i * A.ldx + j0 + q] = make_float4(xrh, xih, xrl, xil);
+                        }
                     }
                     if (MOM) {
                         dw_mac(uu_s[q], uu_e[q], u[q].x, u[q].z, u[q].x, u[q].z);
@@ -332,13 +368,13 @@ __global__ void k_prepare_values_dw(SellView<double> H, int64_t n_pos, double al
 
 namespace {
 
-template <int NB, int VPT, bool MOM, int CH, bool LAST, bool EARLY>
+template <int NB, int VPT, int KIND, bool MOM, int CH, bool LAST>
 cfd_status launch_dw_t(const StepArgs<double> &A, int grid_cap, cudaStream_t stream) {
     const int slots_cap = A.H.slots_bound << A.H.log2C;
     if (slots_cap <= 0) return fail(CFD_ERR_ARG, "matrix has no slot bound; cannot stage");
     const size_t smem = 2 * round_up((size_t)slots_cap * 4, 16) + round_up(2 * (size_t)slots_cap * sizeof(float2), 16);
     if (smem > 200 * 1024) return fail(CFD_ERR_ARG, "chunk too large to stage (%zu bytes)", smem);
-    auto kern = k_cheb_step_dw<NB, VPT, MOM, CH, LAST, EARLY>;
+    auto kern = k_cheb_step_dw<NB, VPT, KIND, MOM, CH, LAST>;
     struct Cache {
         std::mutex mu;
         int occ[64];
@@ -375,42 +411,43 @@ cfd_status launch_dw_t(const StepArgs<double> &A, int grid_cap, cudaStream_t str
 }
 
 template <int NB, int VPT, bool MOM>
-cfd_status launch_dw_m(const StepArgs<double> &A, bool last, bool early, int grid_cap, cudaStream_t s) {
+cfd_status launch_dw_m(int kind, const StepArgs<double> &A, bool last, int grid_cap, cudaStream_t s) {
     // chunk height 32 compiled in when the gathers' 16-byte offsets fit in 32 bits
     const bool fixed = A.H.log2C == 5 && (uint64_t)A.H.n_rows * (uint64_t)A.ldin < (1ULL << 32);
-#define CFD_DW_L(CH_)                                                                            \
-    if (early) return last ? launch_dw_t<NB, VPT, MOM, CH_, true, true>(A, grid_cap, s)           \
-                           : launch_dw_t<NB, VPT, MOM, CH_, false, true>(A, grid_cap, s);          \
-    return last ? launch_dw_t<NB, VPT, MOM, CH_, true, false>(A, grid_cap, s)                     \
-                : launch_dw_t<NB, VPT, MOM, CH_, false, false>(A, grid_cap, s);
+#define CFD_DW_K(CH_)                                                                                  \
+    if (kind == STEP_FIRST) return launch_dw_t<NB, VPT, STEP_FIRST, MOM, CH_, false>(A, grid_cap, s);  \
+    if (kind == STEP_SECOND) return launch_dw_t<NB, VPT, STEP_SECOND, MOM, CH_, false>(A, grid_cap, s); \
+    return last ? launch_dw_t<NB, VPT, STEP_GENERAL, MOM, CH_, true>(A, grid_cap, s)                   \
+                : launch_dw_t<NB, VPT, STEP_GENERAL, MOM, CH_, false>(A, grid_cap, s);
     if (fixed) {
-        CFD_DW_L(32)
+        CFD_DW_K(32)
     }
-    CFD_DW_L(0)
-#undef CFD_DW_L
+    CFD_DW_K(0)
+#undef CFD_DW_K
 }
 
 }  // namespace
 
-// vpt: the native step's default for complex double (1 at n_b = 8, else 2)
-// or that value given explicitly.  early: the epilogue loads before the
-// gathers (the gather = 16 option), else after the row sum.
-cfd_status launch_step_dw(int nb, int vpt, const StepArgs<double> &A, bool last, int grid_cap, cudaStream_t s) {
+// vpt: vectors per thread, as for the native step (default 1 at n_b = 8,
+// else 2; 1 also at n_b = 16 and 32).  last (general steps): X written back
+// as complex double.
+cfd_status launch_step_dw(int kind, int nb, int vpt, const StepArgs<double> &A, bool last, int grid_cap,
+                          cudaStream_t s) {
     if (!A.H.packed) return fail(CFD_ERR_ARG, "double-word arithmetic needs packed matrix values (CFD_PACK_RI)");
     if (!A.status || !A.prep_val) return fail(CFD_ERR_INTERNAL, "double-word step without status or prepared values");
     const bool mom = A.dots != nullptr;
-    const bool early = A.gather >= STEP_GATHER_ALL;
 #define CFD_DW_CASE(NB_, VPT_)                                                                   \
     if (nb == NB_ && vpt == VPT_)                                                                \
-        return mom ? launch_dw_m<NB_, VPT_, true>(A, last, early, grid_cap, s)                   \
-                   : launch_dw_m<NB_, VPT_, false>(A, last, early, grid_cap, s);
+        return mom ? launch_dw_m<NB_, VPT_, true>(kind, A, last, grid_cap, s)                    \
+                   : launch_dw_m<NB_, VPT_, false>(kind, A, last, grid_cap, s);
     CFD_DW_CASE(8, 1)
+    CFD_DW_CASE(16, 1)
     CFD_DW_CASE(16, 2)
+    CFD_DW_CASE(32, 1)
     CFD_DW_CASE(32, 2)
     CFD_DW_CASE(64, 2)
 #undef CFD_DW_CASE
-    return fail(CFD_ERR_ARG, "double-word step: n_b=%d with %d vectors per thread is not built (vpt 1 at n_b = 8, "
-                "else 2)", nb, vpt);
+    return fail(CFD_ERR_ARG, "double-word step: n_b=%d with %d vectors per thread is not built", nb, vpt);
 }
 
 cfd_status launch_dw_convert(void *p, int64_t ld, int64_t n_rows, int nb, bool to_dw, cudaStream_t stream) {

@@ -10,6 +10,16 @@
 
 #include "filter.cuh"
 
+// Gathers of a row in flight together in the grouped loops, and the CTAs
+// per SM the complex-float staged step's registers are capped for (0: no
+// cap): the tuned values, fixed at compile time.
+#ifndef CFD_STAGED_UNR
+#define CFD_STAGED_UNR 4
+#endif
+#ifndef CFD_STAGED_MINB_F32
+#define CFD_STAGED_MINB_F32 0
+#endif
+
 namespace cfd {
 
 namespace cg = cooperative_groups;
@@ -338,7 +348,7 @@ __device__ __forceinline__ void process_row(const StepArgs<T> &A, int64_t i, con
                                             int log2C, int nre, int len, int j0, const StepCoef<T, KIND> &cf,
                                             MomentAcc<T> (&uu)[VPT], MomentAcc<T> (&wu)[VPT]) {
     using C = cplx_t<T>;
-    constexpr int UNR = 4;
+    constexpr int UNR = CFD_STAGED_UNR;
     static_assert(!PREP || KIND == STEP_GENERAL, "prepared values only in general steps");
     // operands of the epilogue do not depend on the gathers: issue their
     // (streaming) loads first so their latency overlaps the SpMMV
@@ -645,7 +655,8 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
 // the matrix's chunk height, fixed at compile time (packed values; the
 // host launches it only for C == CH and 32-bit gather offsets).
 template <typename T, int NB, int VPT, bool MOM, bool PACK, int KMAX = 0, int CH = 0>
-__global__ void __launch_bounds__(STEP_WARPS * 32, KMAX > 8 ? 2 : (KMAX > 0 ? 3 : 0))
+__global__ void __launch_bounds__(STEP_WARPS * 32,
+                                  KMAX > 8 ? 2 : (KMAX > 0 ? 3 : (sizeof(T) == 4 ? CFD_STAGED_MINB_F32 : 0)))
 k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
     using C = cplx_t<T>;
     using V = typename std::conditional<PACK, T, C>::type;
@@ -700,12 +711,13 @@ k_cheb_step_staged(const StepArgs<T> A, int slots_cap) {
     int k = 0;
     bool ok = true;
     bool prefetched = false;      // thread 0: the next chunk's copies were issued this iteration
-    if (tid == 0 && (int64_t)blockIdx.x < n_chunks) issue(blockIdx.x, 0);
+    const ChunkRange cr = cta_chunks(n_chunks);
+    if (tid == 0 && cr.first < cr.last) issue(cr.first, 0);
     __syncthreads();              // s_len[0] written by thread 0
-    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++k) {
+    for (int64_t c = cr.first; c < cr.last; c += cr.stride, ++k) {
         const int b = k & 1;
-        prefetched = c + gridDim.x < n_chunks;
-        if (tid == 0 && prefetched) issue(c + gridDim.x, b ^ 1);
+        prefetched = c + cr.stride < cr.last;
+        if (tid == 0 && prefetched) issue(c + cr.stride, b ^ 1);
         // every thread waits for the chunk's copies itself; a thread whose
         // wait expired skips the chunk, and the barrier below then stops all
         const bool landed = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), limit);

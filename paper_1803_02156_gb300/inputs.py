@@ -75,3 +75,15 @@ def gaussian_block_device(N, n_s, seed, dtype=None, device="cuda"):
     z = torch.randn(N, n_s, 2, generator=g, device=device, dtype=real) * (0.5 ** 0.5)
     return torch.view_as_complex(z).contiguous()
 
+
+def fill_gaussian_device(X, seed):
+    """Overwrite the complex device tensor X (contiguous) in place with the
+    values gaussian_block_device(X.shape[0], X.shape[1], seed, X.dtype) draws,
+    without allocating a second block."""
+    import torch
+    g = torch.Generator(device=X.device)
+    g.manual_seed(int(seed))
+    r = torch.view_as_real(X)
+    torch.randn(r.shape, generator=g, device=X.device, dtype=r.dtype, out=r)
+    r.mul_(0.5 ** 0.5)
+    return X

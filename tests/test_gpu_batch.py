@@ -126,6 +126,67 @@ def test_persistent_and_options_bitwise(b, prec, n_b, vpt):
     assert (torch.linalg.norm(Y - ref) / torch.linalg.norm(ref)).item() < tol
 
 
+@pytest.mark.parametrize("prec,n_b", [("c64p", 32), ("c64p", 16), ("c128p", 32), ("c128p", 64)])
+def test_persistent_staged_equals_per_step(b, prec, n_b):
+    """With packed values the persistent filter runs steps 1 and 2 as single
+    launches and steps 3..n_p in one cooperative launch of the staged step:
+    bit for bit the per-step staged filter (same row arithmetic), also with
+    fewer CTAs than chunks and a ragged last chunk."""
+    import torch
+    dt = torch.complex128 if prec.startswith("c128") else torch.complex64
+    L = (10, 9, 7)
+    H = b.cfd_build_matrix(b.topi_params(*L), 32, 1, prec)
+    X0 = torch.from_numpy(inputs.gaussian_block(H.N, 64, seed=3)).to(dt).cuda()
+    ref = X0.clone()
+    b.cfd_filter(H, -8.6, 8.6, -0.5, 0.5, 80, ref, n_b)
+    for cap in (0, 7):
+        Y = X0.clone()
+        b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 80, Y, n_b, persistent=1, grid_cap=cap)
+        torch.cuda.synchronize()
+        assert torch.equal(Y, ref), cap
+
+
+def test_persistent_staged_batched_equals_looped(b):
+    """The batched filter with the staged persistent launch (packed complex64
+    batch) equals the per-realisation filter bit for bit."""
+    import torch
+    B = b.cfd_build_batch(_params(b), 32, 1, "c64p")
+    wt, w = _windows(b)
+    n_s, n_b, n_p = 16, 16, 60
+    X = torch.zeros(B.N, n_s, dtype=torch.complex64, device="cuda")
+    blocks = []
+    for r, (nx, ny, nz, s) in enumerate(LATTICES):
+        N = 4 * nx * ny * nz
+        Xr = torch.from_numpy(inputs.gaussian_block(N, n_s, seed=100 + r)).to(torch.complex64).cuda()
+        X[B.row_off[r]:B.row_off[r] + N] = Xr
+        blocks.append(Xr)
+    b.cfd_filter_batched(B, wt, n_p, X, n_b, persistent=1)
+    for r, (nx, ny, nz, s) in enumerate(LATTICES):
+        N = 4 * nx * ny * nz
+        H = b.cfd_build_matrix(b.topi_params(nx, ny, nz, seed=s), 32, 1, "c64p")
+        Y = blocks[r].clone()
+        b.cfd_filter(H, w[r][0], w[r][1], w[r][2], w[r][3], n_p, Y, n_b)
+        assert torch.equal(X[B.row_off[r]:B.row_off[r] + N], Y), r
+
+
+def test_persistent_staged_wait_timeout(b):
+    """The staged persistent launch with its bounded waits made to expire
+    (staged = 2): CFD_ERR_TIMEOUT in the status, every CTA leaves at the same
+    grid barrier, and the context stays usable."""
+    import torch
+    H = b.cfd_build_matrix(b.topi_params(8, 8, 4), 32, 1, "c64p")
+    X = torch.from_numpy(inputs.gaussian_block(H.N, 16, seed=6)).to(torch.complex64).cuda()
+    work = torch.empty(b.cfd_filter_workspace(H.N, 16, 16, 10, "c64", "c64"), dtype=torch.uint8, device="cuda")
+    b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 10, X, 16, persistent=1, staged=2, work=work)
+    with pytest.raises(b.CfdError) as e:
+        b.cfd_workspace_status(work)
+    assert e.value.status == 5
+    assert "still have been in flight" not in str(e.value)
+    Y = X.clone()
+    b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 10, Y, 16, persistent=1, work=work)
+    b.cfd_workspace_status(work)
+
+
 def test_graph_capture_replays_filter(b):
     """The n_p-step recurrence captured as a CUDA graph (torch capture of the
     C-ABI call on a side stream) replays to the same result."""

@@ -83,18 +83,19 @@ def test_dw_full_degree_against_native(b):
     assert (torch.max(torch.abs(md - mn)) / torch.max(torch.abs(mn))).item() < TOL
 
 
-def test_dw_epilogue_order_is_bitwise_equal(b):
-    """Loading X and the own row before or after the gathers (gather = 16 or
-    the default) changes no arithmetic: bitwise equal block; moments equal."""
+@pytest.mark.parametrize("n_b", [16, 32])
+def test_dw_vectors_per_thread_bitwise_equal(b, n_b):
+    """One or two vectors per thread change no element's arithmetic: bitwise
+    equal block; moments equal up to the order of their reduction."""
     import torch
     H = b.cfd_build_matrix(b.topi_params(12, 10, 7), 32, 1, "c128p")
     X0 = torch.from_numpy(inputs.gaussian_block(H.N, 64, seed=9)).cuda()
     Xa, Xb = X0.clone(), X0.clone()
-    ma = b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, 50, Xa, 32, moments=True, arith=1)
-    mb = b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, 50, Xb, 32, moments=True, arith=1, gather=16)
+    ma = b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, 50, Xa, n_b, moments=True, arith=1, vpt=1)
+    mb = b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, 50, Xb, n_b, moments=True, arith=1, vpt=2)
     torch.cuda.synchronize()
     assert torch.equal(Xa, Xb)
-    assert torch.equal(ma, mb)
+    assert (torch.max(torch.abs(ma - mb)) / torch.max(torch.abs(ma))).item() < 1e-13
 
 
 def test_dw_block_width_invariance(b):
