@@ -6,7 +6,12 @@
 // chip-to-chip link; two device block buffers are used in turn: while block b
 // is filtered on the caller's stream, a copy stream writes block b - 1 back
 // and brings block b + 1 in.  Blocks are column windows of the row-major
-// host block, moved with pitched 2-D copies.
+// host block.  Where the GPU can address the host block (page-locked memory,
+// or any host memory on a system with pageable-memory access), a copy kernel
+// moves the windows over the link with coalesced 16-byte loads and stores:
+// every row of a window is one contiguous run of n_b complex values, which a
+// pitched 2-D DMA copy moves as a separate small transfer per row (about
+// 5 GB/s for 512-byte rows).  Otherwise pitched 2-D copies are used.
 
 #include <algorithm>
 
@@ -39,6 +44,42 @@ struct CopyPipe {
     }
 };
 
+// dst rows (stride ldd bytes) <- src rows (stride lds bytes), n_rows rows of
+// width bytes (multiples of 16); grid-stride, four 16-byte moves in flight per
+// thread.
+__global__ void k_copy_rows(const char *src, int64_t lds, char *dst, int64_t ldd, int64_t n_rows, int width) {
+    const int w16 = width >> 4;
+    const int64_t total = n_rows * w16;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; e + 3 * stride < total; e += 4 * stride) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t f = e + u * stride;
+            v[u] = *reinterpret_cast<const uint4 *>(src + (f / w16) * lds + (f % w16) * 16);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t f = e + u * stride;
+            *reinterpret_cast<uint4 *>(dst + (f / w16) * ldd + (f % w16) * 16) = v[u];
+        }
+    }
+    for (; e < total; e += stride)
+        *reinterpret_cast<uint4 *>(dst + (e / w16) * ldd + (e % w16) * 16) =
+            *reinterpret_cast<const uint4 *>(src + (e / w16) * lds + (e % w16) * 16);
+}
+
+cfd_status copy_rows(const void *src, int64_t lds, void *dst, int64_t ldd, int64_t n_rows, size_t width,
+                     cudaStream_t stream) {
+    const int grid = 2 * sm_count();
+    k_copy_rows<<<grid, 256, 0, stream>>>(static_cast<const char *>(src), lds, static_cast<char *>(dst), ldd, n_rows,
+                                          (int)width);
+    CFD_COUNT_LAUNCH();
+    CFD_LAUNCH_CHECK();
+    return CFD_OK;
+}
+
 }  // namespace
 
 }  // namespace cfd
@@ -65,6 +106,16 @@ static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax
     CFD_CUDA(cudaPointerGetAttributes(&pa, X.ptr));
     if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)
         return fail(CFD_ERR_ARG, "X must be host memory (use cfd_filter for device blocks)");
+    // the host block's address as the GPU sees it, if it can address it
+    char *host_dev = nullptr;
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+        host_dev = static_cast<char *>(pa.devicePointer);
+    } else {
+        int dev = 0, pageable = 0;
+        CFD_CUDA(cudaGetDevice(&dev));
+        CFD_CUDA(cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev));
+        if (pageable) host_dev = static_cast<char *>(X.ptr);
+    }
     const size_t need = host_filter_workspace(H->n_rows, n_b, n_p, H->prec, X.prec);
     if (work_bytes < need) return fail(CFD_ERR_OOM, "host filter workspace %zu < %zu bytes", work_bytes, need);
 
@@ -83,8 +134,12 @@ static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax
     CFD_CUDA(cudaEventRecord(cp.start, stream));
     CFD_CUDA(cudaStreamWaitEvent(cp.copy, cp.start, 0));
     auto bring_in = [&](int b) -> cfd_status {
-        CFD_CUDA(cudaMemcpy2DAsync(dbuf[b & 1], width, host + (size_t)b * width, hpitch, width, (size_t)N,
-                                   cudaMemcpyHostToDevice, cp.copy));
+        if (host_dev)
+            CFD_TRY(copy_rows(host_dev + (size_t)b * width, (int64_t)hpitch, dbuf[b & 1], (int64_t)width, N, width,
+                              cp.copy));
+        else
+            CFD_CUDA(cudaMemcpy2DAsync(dbuf[b & 1], width, host + (size_t)b * width, hpitch, width, (size_t)N,
+                                       cudaMemcpyHostToDevice, cp.copy));
         CFD_CUDA(cudaEventRecord(cp.in[b & 1], cp.copy));
         return CFD_OK;
     };
@@ -101,8 +156,12 @@ static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax
         CFD_CUDA(cudaEventRecord(cp.done[b & 1], stream));
         // write block b back, then reuse its buffer for block b + 2
         CFD_CUDA(cudaStreamWaitEvent(cp.copy, cp.done[b & 1], 0));
-        CFD_CUDA(cudaMemcpy2DAsync(host + (size_t)b * width, hpitch, dbuf[b & 1], width, width, (size_t)N,
-                                   cudaMemcpyDeviceToHost, cp.copy));
+        if (host_dev)
+            CFD_TRY(copy_rows(dbuf[b & 1], (int64_t)width, host_dev + (size_t)b * width, (int64_t)hpitch, N, width,
+                              cp.copy));
+        else
+            CFD_CUDA(cudaMemcpy2DAsync(host + (size_t)b * width, hpitch, dbuf[b & 1], width, width, (size_t)N,
+                                       cudaMemcpyDeviceToHost, cp.copy));
         if (b + 2 < n_blocks) CFD_TRY(bring_in(b + 2));
     }
     // later work on `stream` sees the whole search space written back
