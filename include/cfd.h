@@ -479,6 +479,97 @@ cfd_status cfd_filter_noalloc_status(cudaStream_t stream);
 
 
 /* ------------------------------------------------------------------------ */
+/* Distributed filter: z-slabs with halo exchange (Sect. 6, Algorithms 3, 4) */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One rank's share of a Topi lattice distributed over nranks processes
+ * (Sect. 6: every process works on a contiguous set of matrix rows and the
+ * matching rows of the block vectors; the matrix's stencil structure makes
+ * the exchange nearest-neighbour).  Ranks own consecutive z-planes, planes
+ * [z0, z1) = rows [row0, row0 + n_local), z0 = rank Nz / nranks.  A rank's
+ * local matrix numbers its columns own rows first (0 .. n_local - 1), then
+ * the lower halo plane (n_local .. n_local + plane - 1: the plane below z0,
+ * owned by lo_rank) and the upper halo plane (the next plane: the one above
+ * z1 - 1, owned by hi_rank); a missing neighbour (open z, or one rank) has
+ * rank -1 and base -1.  With periodic z the first and last ranks are
+ * neighbours.
+ */
+typedef struct cfd_slab {
+    int32_t nranks, rank;
+    int32_t z0, z1;
+    int64_t row0, n_local, plane;
+    int32_t lo_rank, hi_rank;
+    int64_t lo_base, hi_base;   /* first canonical row of the lower / upper halo plane */
+} cfd_slab;
+
+/* The slab of `rank` among nranks (1 <= nranks <= Nz).  Host only. */
+cfd_status cfd_slab_plan(const cfd_topi_params *p, int nranks, int rank, cfd_slab *out);
+
+/* Local column of canonical column col in the slab's numbering (-1 if the
+ * slab's rows never reference it).  Host only. */
+int64_t cfd_slab_local_col(const cfd_slab *s, int64_t col);
+
+/* Sizes / build of the slab's rows of Topi (as cfd_matrix_query_size and
+ * cfd_build_matrix): n_rows = n_local, columns in the slab's numbering.  Each
+ * row keeps the entries in the order of the canonical matrix's row, so a
+ * slab's row sums are bit for bit those of the whole matrix. */
+cfd_status cfd_slab_query_size(const cfd_topi_params *p, const cfd_slab *s, int C, int sigma, int prec,
+                               cfd_matrix_sizes *out);
+cfd_status cfd_build_matrix_slab(const cfd_topi_params *p, const cfd_slab *s, int C, int sigma, int prec,
+                                 const cfd_matrix_buffers *buf, cfd_matrix *out, cudaStream_t stream);
+
+/*
+ * Device scratch bytes of one slab's share of the distributed filter (the
+ * filter scratch, and the recurrence blocks with their halo rows: one pair,
+ * or one pair per subspace block for the pipelined mode).  mode: 0 vector
+ * mode (Algorithm 3), 1 pipelined mode (Algorithm 4).
+ */
+size_t cfd_filter_slab_workspace(const cfd_slab *s, int n_s, int n_b, int n_p, int prec, int mode);
+
+/*
+ * The filter (as cfd_filter) distributed over the nranks slabs of one
+ * lattice, all held in this process on the current device: slabs[r] is
+ * rank r's plan, H[r] its slab matrix, X[r] its n_local x n_s block (same
+ * precision as H), work[r] its scratch (work_bytes each).  Before every
+ * fused step the boundary planes of the gathered block are copied into the
+ * neighbours' halo rows (the exchange of Sect. 6 done by device copies), so
+ * each slab's filtered rows are bit for bit those of cfd_filter on the whole
+ * matrix.  mode 0 (vector mode, Algorithm 3): block by block, exchange then
+ * step; mode 1 (pipelined mode, Algorithm 4): all blocks advance one degree
+ * at a time and the exchange of block b + 1 runs on a second stream while
+ * block b computes.  moments (device, nullable, [n_s][2 n_p]): the moments of
+ * the whole vectors (per-slab dots summed).  opts: vpt and arith are used.
+ * Asynchronous on `stream`.
+ */
+cfd_status cfd_filter_slabs(int nranks, const cfd_slab *slabs, const cfd_matrix *const *H, double lmin, double lmax,
+                            double lam_l, double lam_r, int n_p, const cfd_block *X, int n_b, int mode,
+                            void *const *work, size_t work_bytes, double *moments, const cfd_filter_opts *opts,
+                            cudaStream_t stream);
+
+/* NCCL communicator for cfd_filter_slab_nccl (libnccl is loaded at first use;
+ * CFD_ERR_ARG if it cannot be).  id: 128 bytes, made on one rank by
+ * cfd_nccl_unique_id and given to every rank (e.g. through
+ * torch.distributed); comm receives the opaque communicator. */
+cfd_status cfd_nccl_unique_id(void *id);
+cfd_status cfd_nccl_comm_init(const void *id, int nranks, int rank, void **comm);
+cfd_status cfd_nccl_comm_destroy(void *comm);
+
+/*
+ * One rank's part of the distributed filter, one slab per process and GPU:
+ * the halo planes are exchanged with NCCL point-to-point transfers on
+ * `stream` (every rank posts: its top plane to hi_rank, its bottom plane to
+ * lo_rank, the lower halo from lo_rank, the upper halo from hi_rank) and the
+ * moment dots are summed with an NCCL all-reduce, so every rank receives the
+ * moments of the whole vectors.  Arguments otherwise as cfd_filter_slabs for
+ * one slab.  Every rank must make the call with the same n_s, n_b, n_p, mode
+ * and window.
+ */
+cfd_status cfd_filter_slab_nccl(const cfd_slab *slab, const cfd_matrix *H, double lmin, double lmax, double lam_l,
+                                double lam_r, int n_p, cfd_block X, int n_b, int mode, void *work, size_t work_bytes,
+                                double *moments, const cfd_filter_opts *opts, void *comm, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Spectral bounds                                                           */
 /* ------------------------------------------------------------------------ */
 

@@ -83,7 +83,15 @@ class cfd_solve_result(ctypes.Structure):
                 ("t_total", ctypes.c_double)]
 
 
+class cfd_slab(ctypes.Structure):
+    _fields_ = [("nranks", ctypes.c_int32), ("rank", ctypes.c_int32), ("z0", ctypes.c_int32), ("z1", ctypes.c_int32),
+                ("row0", ctypes.c_int64), ("n_local", ctypes.c_int64), ("plane", ctypes.c_int64),
+                ("lo_rank", ctypes.c_int32), ("hi_rank", ctypes.c_int32), ("lo_base", ctypes.c_int64),
+                ("hi_base", ctypes.c_int64)]
+
+
 CFD_POLICY_FP64, CFD_POLICY_MIXED, CFD_POLICY_FP64_DW, CFD_POLICY_MIXED_DW = 0, 1, 2, 3
+CFD_DIST_VECTOR, CFD_DIST_PIPELINED = 0, 1
 
 # ---------------------------------------------------------------- load --
 
@@ -182,6 +190,30 @@ _PROTOS = {
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block,
                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "cfd_filter_noalloc_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "cfd_slab_plan": (ctypes.c_int, [ctypes.POINTER(cfd_topi_params), ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(cfd_slab)]),
+    "cfd_slab_local_col": (ctypes.c_int64, [ctypes.POINTER(cfd_slab), ctypes.c_int64]),
+    "cfd_slab_query_size": (ctypes.c_int, [ctypes.POINTER(cfd_topi_params), ctypes.POINTER(cfd_slab), ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(cfd_matrix_sizes)]),
+    "cfd_build_matrix_slab": (ctypes.c_int, [ctypes.POINTER(cfd_topi_params), ctypes.POINTER(cfd_slab), ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, ctypes.POINTER(cfd_matrix_buffers),
+                                             ctypes.POINTER(cfd_matrix), ctypes.c_void_p]),
+    "cfd_filter_slab_workspace": (ctypes.c_size_t, [ctypes.POINTER(cfd_slab), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_int, ctypes.c_int]),
+    "cfd_filter_slabs": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(cfd_slab), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.POINTER(cfd_block), ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_void_p,
+                                        ctypes.POINTER(cfd_filter_opts), ctypes.c_void_p]),
+    "cfd_nccl_unique_id": (ctypes.c_int, [ctypes.c_void_p]),
+    "cfd_nccl_comm_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "cfd_nccl_comm_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "cfd_filter_slab_nccl": (ctypes.c_int, [ctypes.POINTER(cfd_slab), ctypes.POINTER(cfd_matrix), ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            cfd_block, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(cfd_filter_opts),
+                                            ctypes.c_void_p, ctypes.c_void_p]),
     "cfd_probe_fma_workspace": (ctypes.c_size_t, []),
     "cfd_probe_fma": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
                                      ctypes.c_size_t, ctypes.c_void_p]),
@@ -636,3 +668,92 @@ def cfd_probe_fma(prec="c128", iters=1 << 16, device="cuda", stream=None):
     _check(lib().cfd_probe_fma(_prec(prec), int(iters), ctypes.byref(out), _ptr(work), work.numel(),
                                _stream(stream)))
     return out.value
+
+
+# ------------------------------------------------- distributed (z-slabs) --
+
+def cfd_slab_plan(params, nranks, rank):
+    """The z-slab of `rank` among nranks (host only)."""
+    out = cfd_slab()
+    _check(lib().cfd_slab_plan(ctypes.byref(params), nranks, rank, ctypes.byref(out)))
+    return out
+
+
+def cfd_slab_local_col(slab, col):
+    return int(lib().cfd_slab_local_col(ctypes.byref(slab), int(col)))
+
+
+def cfd_build_matrix_slab(params, slab, C=32, sigma=1, prec="c128", device="cuda", stream=None):
+    """Allocate and build one slab's rows of Topi (columns in the slab's numbering)."""
+    prec = _prec(prec)
+    sz = cfd_matrix_sizes()
+    _check(lib().cfd_slab_query_size(ctypes.byref(params), ctypes.byref(slab), C, sigma, prec, ctypes.byref(sz)))
+    dev = torch.device(device)
+    bufs = {
+        "val": _workspace(sz.bytes_val, dev), "col": _workspace(sz.bytes_col, dev),
+        "chunk_ptr": _workspace(sz.bytes_chunk_ptr, dev), "chunk_len": _workspace(sz.bytes_chunk_len, dev),
+        "perm": _workspace(sz.bytes_perm, dev) if sz.bytes_perm else None,
+        "work": _workspace(sz.bytes_work, dev),
+    }
+    b = cfd_matrix_buffers(*[(bufs[k].data_ptr() if bufs[k] is not None else None)
+                             for k in ("val", "col", "chunk_ptr", "chunk_len", "perm", "work")])
+    out = cfd_matrix()
+    _check(lib().cfd_build_matrix_slab(ctypes.byref(params), ctypes.byref(slab), C, sigma, prec, ctypes.byref(b),
+                                       ctypes.byref(out), _stream(stream)))
+    return Matrix(out, bufs, params)
+
+
+def cfd_filter_slabs(slabs, Hs, lmin, lmax, lam_l, lam_r, n_p, Xs, n_b, mode=CFD_DIST_VECTOR, moments=False,
+                     arith=0, stream=None):
+    """The distributed filter with every slab in this process (halo exchange by
+    device copies).  Xs: the slabs' local blocks (filtered in place).  Returns
+    the moments of the whole vectors when moments=True."""
+    n = len(slabs)
+    S = (cfd_slab * n)(*slabs)
+    blks = [block_of(X) for X in Xs]
+    B = (cfd_block * n)(*blks)
+    Hp = (ctypes.c_void_p * n)(*[ctypes.addressof(H.c) for H in Hs])
+    ws = max(lib().cfd_filter_slab_workspace(ctypes.byref(slabs[r]), blks[r].n_cols, n_b, n_p, Hs[r].prec, mode)
+             for r in range(n))
+    works = [_workspace(ws, Xs[0].device) for _ in range(n)]
+    W = (ctypes.c_void_p * n)(*[w.data_ptr() for w in works])
+    mu = torch.empty(blks[0].n_cols, 2 * n_p, dtype=torch.float64, device=Xs[0].device) if moments else None
+    o = cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0)
+    _check(lib().cfd_filter_slabs(n, S, Hp, lmin, lmax, lam_l, lam_r, n_p, B, n_b, mode, W, ws, _ptr(mu),
+                                  ctypes.byref(o), _stream(stream)))
+    (stream or torch.cuda.current_stream()).synchronize()      # the workspaces are freed on return
+    del works
+    return mu
+
+
+def cfd_nccl_unique_id():
+    """128-byte NCCL unique id (bytes), to be shared with every rank."""
+    buf = ctypes.create_string_buffer(128)
+    _check(lib().cfd_nccl_unique_id(buf))
+    return buf.raw
+
+
+def cfd_nccl_comm_init(uid, nranks, rank):
+    comm = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(bytes(uid), 128)
+    _check(lib().cfd_nccl_comm_init(buf, nranks, rank, ctypes.byref(comm)))
+    return comm
+
+
+def cfd_nccl_comm_destroy(comm):
+    _check(lib().cfd_nccl_comm_destroy(comm))
+
+
+def cfd_filter_slab_nccl(slab, H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, comm, mode=CFD_DIST_VECTOR,
+                         moments=False, arith=0, work=None, stream=None):
+    """One rank's part of the distributed filter (one slab per process and GPU,
+    halo exchange over NCCL).  Every rank receives the global moments."""
+    blk = block_of(X)
+    ws = lib().cfd_filter_slab_workspace(ctypes.byref(slab), blk.n_cols, n_b, n_p, H.prec, mode)
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, X.device)
+    mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=X.device) if moments else None
+    o = cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0)
+    _check(lib().cfd_filter_slab_nccl(ctypes.byref(slab), H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, mode,
+                                      _ptr(work), work.numel(), _ptr(mu), ctypes.byref(o), comm, _stream(stream)))
+    return mu

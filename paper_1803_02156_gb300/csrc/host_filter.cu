@@ -37,7 +37,10 @@ struct CopyPipe {
         if (copy) cudaStreamDestroy(copy);
     }
     cfd_status create() {
-        CFD_CUDA(cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
+        // the copies' CTAs are scheduled ahead of the filter's when SM slots free up
+        int lo = 0, hi = 0;
+        CFD_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CFD_CUDA(cudaStreamCreateWithPriority(&copy, cudaStreamNonBlocking, hi));
         for (cudaEvent_t *e : {&start, &in[0], &in[1], &done[0], &done[1], &out})
             CFD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         return CFD_OK;
@@ -45,36 +48,39 @@ struct CopyPipe {
 };
 
 // dst rows (stride ldd bytes) <- src rows (stride lds bytes), n_rows rows of
-// width bytes (multiples of 16); grid-stride, four 16-byte moves in flight per
-// thread.
-__global__ void k_copy_rows(const char *src, int64_t lds, char *dst, int64_t ldd, int64_t n_rows, int width) {
+// width bytes (multiples of 16).  Each CTA moves one small span (four
+// 16-byte moves per thread) and exits, so while the filter's full-wave step
+// launches hold the SMs, copy CTAs still get the slots that free up between
+// them (a few long-lived copy CTAs would hold their share of the copy back).
+constexpr int kCopyThreads = 256;
+constexpr int kCopyPerThread = 4;
+
+__global__ void __launch_bounds__(kCopyThreads)
+k_copy_rows(const char *src, int64_t lds, char *dst, int64_t ldd, int64_t n_rows, int width) {
     const int w16 = width >> 4;
     const int64_t total = n_rows * w16;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    for (; e + 3 * stride < total; e += 4 * stride) {
-        uint4 v[4];
+    const int64_t e0 = (int64_t)blockIdx.x * (kCopyThreads * kCopyPerThread) + threadIdx.x;
+    uint4 v[kCopyPerThread];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t f = e + u * stride;
-            v[u] = *reinterpret_cast<const uint4 *>(src + (f / w16) * lds + (f % w16) * 16);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t f = e + u * stride;
-            *reinterpret_cast<uint4 *>(dst + (f / w16) * ldd + (f % w16) * 16) = v[u];
-        }
+    for (int u = 0; u < kCopyPerThread; ++u) {
+        const int64_t f = e0 + u * kCopyThreads;
+        if (f < total) v[u] = *reinterpret_cast<const uint4 *>(src + (f / w16) * lds + (f % w16) * 16);
     }
-    for (; e < total; e += stride)
-        *reinterpret_cast<uint4 *>(dst + (e / w16) * ldd + (e % w16) * 16) =
-            *reinterpret_cast<const uint4 *>(src + (e / w16) * lds + (e % w16) * 16);
+#pragma unroll
+    for (int u = 0; u < kCopyPerThread; ++u) {
+        const int64_t f = e0 + u * kCopyThreads;
+        if (f < total) *reinterpret_cast<uint4 *>(dst + (f / w16) * ldd + (f % w16) * 16) = v[u];
+    }
 }
 
 cfd_status copy_rows(const void *src, int64_t lds, void *dst, int64_t ldd, int64_t n_rows, size_t width,
                      cudaStream_t stream) {
-    const int grid = 2 * sm_count();
-    k_copy_rows<<<grid, 256, 0, stream>>>(static_cast<const char *>(src), lds, static_cast<char *>(dst), ldd, n_rows,
-                                          (int)width);
+    const int64_t total = n_rows * (int64_t)(width >> 4);
+    const int64_t grid = (total + kCopyThreads * kCopyPerThread - 1) / (kCopyThreads * kCopyPerThread);
+    if (grid == 0) return CFD_OK;
+    if (grid > 2147483647LL) return fail(CFD_ERR_ARG, "block too large to copy (%lld rows)", (long long)n_rows);
+    k_copy_rows<<<(unsigned)grid, kCopyThreads, 0, stream>>>(static_cast<const char *>(src), lds,
+                                                             static_cast<char *>(dst), ldd, n_rows, (int)width);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;

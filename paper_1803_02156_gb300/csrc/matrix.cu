@@ -10,10 +10,16 @@ namespace {
 
 constexpr int TOPI_MAX_ROW = 13;
 
+// The lattice, and the rows built: all of them, or the rows [row0, row0 +
+// n_rows) of one z-slab, whose columns are then renumbered locally (own rows
+// first, then the lower and the upper halo plane; cfd_slab_local_col).
 struct Lattice {
     int32_t L[3];
     int32_t per[3];
-    int64_t n_rows;
+    int64_t n_rows;              // rows built
+    int64_t row0 = 0;            // canonical index of built row 0
+    int32_t slab = 0;            // 1: renumber columns as a slab
+    int64_t plane = 0, lo_base = -1, hi_base = -1;
 };
 
 Lattice lattice_of(const cfd_topi_params *p) {
@@ -26,6 +32,26 @@ Lattice lattice_of(const cfd_topi_params *p) {
     g.per[2] = p->periodic_z != 0;
     g.n_rows = 4LL * p->Nx * p->Ny * p->Nz;
     return g;
+}
+
+Lattice lattice_of_slab(const cfd_topi_params *p, const cfd_slab *s) {
+    Lattice g = lattice_of(p);
+    g.n_rows = s->n_local;
+    g.row0 = s->row0;
+    g.slab = 1;
+    g.plane = s->plane;
+    g.lo_base = s->lo_base;
+    g.hi_base = s->hi_base;
+    return g;
+}
+
+// Column of canonical index c in the built rows' numbering.
+__host__ __device__ inline int64_t local_col(int64_t c, const Lattice &g) {
+    if (!g.slab) return c;
+    if (c >= g.row0 && c < g.row0 + g.n_rows) return c - g.row0;
+    if (g.lo_base >= 0 && c >= g.lo_base && c < g.lo_base + g.plane) return g.n_rows + (c - g.lo_base);
+    if (g.hi_base >= 0 && c >= g.hi_base && c < g.hi_base + g.plane) return g.n_rows + g.plane + (c - g.hi_base);
+    return -1;
 }
 
 // Stored entries of canonical row i: one on-site entry and two per existing
@@ -164,14 +190,14 @@ __global__ void k_sigma_sort(Lattice g, int sigma, int32_t *perm) {
     int64_t r1 = min(r0 + (int64_t)sigma, g.n_rows);
     int cnt[TOPI_MAX_ROW + 1];
     for (int k = 0; k <= TOPI_MAX_ROW; ++k) cnt[k] = 0;
-    for (int64_t i = r0; i < r1; ++i) ++cnt[topi_row_len(i, g)];
+    for (int64_t i = r0; i < r1; ++i) ++cnt[topi_row_len(g.row0 + i, g)];
     int start[TOPI_MAX_ROW + 1];
     int run = 0;
     for (int k = TOPI_MAX_ROW; k >= 0; --k) {
         start[k] = run;
         run += cnt[k];
     }
-    for (int64_t i = r0; i < r1; ++i) perm[r0 + start[topi_row_len(i, g)]++] = (int32_t)i;
+    for (int64_t i = r0; i < r1; ++i) perm[r0 + start[topi_row_len(g.row0 + i, g)]++] = (int32_t)i;
 }
 
 // Slots per row of each chunk: the longest row's length, or for packed
@@ -186,7 +212,7 @@ __global__ void k_chunk_len(Lattice g, int log2C, int64_t n_chunks, const int32_
     for (int rr = 0; rr < C; ++rr) {
         int64_t r = (c << log2C) + rr;
         if (r >= g.n_rows) break;
-        int64_t i = perm ? perm[r] : r;
+        int64_t i = g.row0 + (perm ? perm[r] : r);
         mx = max(mx, topi_row_len(i, g));
         int a, b;
         topi_row_counts(i, g, &a, &b);
@@ -209,7 +235,8 @@ __global__ void k_fill(Lattice g, TopiValues v, int log2C, int64_t n_chunks, con
     int32_t ec[TOPI_MAX_ROW];
     double2 ev[TOPI_MAX_ROW];
     int n = 0;
-    if (r < g.n_rows) n = topi_row(perm ? perm[r] : r, g, v, ec, ev);
+    if (r < g.n_rows) n = topi_row(g.row0 + (perm ? perm[r] : r), g, v, ec, ev);
+    for (int k = 0; k < n; ++k) ec[k] = (int32_t)local_col(ec[k], g);
     for (int k = 0; k < len; ++k) {
         int64_t at = base + ((int64_t)k << log2C);
         if (k < n) {
@@ -238,7 +265,8 @@ __global__ void k_fill_packed(Lattice g, TopiValues v, int log2C, int64_t n_chun
     int32_t ec[TOPI_MAX_ROW];
     double2 ev[TOPI_MAX_ROW];
     int n = 0;
-    if (r < g.n_rows) n = topi_row(perm ? perm[r] : r, g, v, ec, ev);
+    if (r < g.n_rows) n = topi_row(g.row0 + (perm ? perm[r] : r), g, v, ec, ev);
+    for (int k = 0; k < n; ++k) ec[k] = (int32_t)local_col(ec[k], g);
     int kre = 0, kim = n_re;
     for (int k = 0; k < n; ++k) {
         bool im = ev[k].y != 0.0;
@@ -355,12 +383,12 @@ int64_t host_slots(const Lattice &g, int C, int sigma, bool packed) {
         if (sigma > 1) {
             for (int k = TOPI_MAX_ROW; k >= 0; --k)
                 for (int64_t i = r0; i < r1; ++i)
-                    if (topi_row_len(i, g) == k) order.push_back(i);
+                    if (topi_row_len(g.row0 + i, g) == k) order.push_back(i);
         }
         for (int64_t a = r0; a < r1; a += C) {
             int mx = 0, mre = 0, mim = 0;
             for (int64_t q = a; q < std::min<int64_t>(a + C, r1); ++q) {
-                int64_t i = sigma > 1 ? order[q - r0] : q;
+                int64_t i = g.row0 + (sigma > 1 ? order[q - r0] : q);
                 mx = std::max(mx, topi_row_len(i, g));
                 int x, y;
                 topi_row_counts(i, g, &x, &y);
@@ -422,43 +450,31 @@ cfd_status batch_layout(const cfd_topi_params *p, int R, int C, int sigma, int p
     return CFD_OK;
 }
 
-}  // namespace
-}  // namespace cfd
-
-using namespace cfd;
-
-extern "C" {
-
-cfd_status cfd_matrix_query_size(const cfd_topi_params *p, int C, int sigma, int prec_arg,
-                                 cfd_matrix_sizes *out) {
-    clear_error();
+// Sizes of the SELL arrays for the rows of g.
+void query_sizes(const Lattice &g, int C, int sigma, int prec_arg, cfd_matrix_sizes *out) {
     const bool packed = (prec_arg & CFD_PACK_RI) != 0;
     const int prec = prec_arg & ~CFD_PACK_RI;
-    CFD_TRY(check_params(p, C, sigma, prec));
-    if (!out) return fail(CFD_ERR_ARG, "out is NULL");
-    Lattice g = lattice_of(p);
     int64_t nnz = 0;
-    for (int64_t i = 0; i < g.n_rows; i += 4) nnz += 4 * topi_row_len(i, g);
+    for (int64_t i = 0; i < g.n_rows; i += 4) nnz += 4 * topi_row_len(g.row0 + i, g);
     int64_t n_chunks = (g.n_rows + C - 1) / C;
     int64_t slots = host_slots(g, C, sigma, packed);
-    size_t s = packed ? ((prec == CFD_C128) ? 8 : 4) : ((prec == CFD_C128) ? 16 : 8);
+    size_t sv = packed ? ((prec == CFD_C128) ? 8 : 4) : ((prec == CFD_C128) ? 16 : 8);
     out->n_rows = g.n_rows;
     out->nnz = nnz;
     out->n_chunks = n_chunks;
     out->n_slots = slots;
-    out->bytes_val = (int64_t)round_up((size_t)slots * s, 256);
+    out->bytes_val = (int64_t)round_up((size_t)slots * sv, 256);
     out->bytes_col = (int64_t)round_up((size_t)slots * 4, 256);
     out->bytes_chunk_ptr = (int64_t)round_up((size_t)(n_chunks + 1) * 8, 256);
     out->bytes_chunk_len = (int64_t)round_up((size_t)n_chunks * 4, 256);
     out->bytes_perm = sigma > 1 ? (int64_t)round_up((size_t)g.n_rows * 4, 256) : 0;
     out->bytes_work = (int64_t)(round_up((size_t)n_chunks * 8, 256) + scan_workspace(n_chunks));
-    return CFD_OK;
 }
 
-cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec_arg,
-                            const cfd_matrix_buffers *buf, cfd_matrix *out, cudaStream_t stream) {
-    cfd_matrix_sizes sz;
-    CFD_TRY(cfd_matrix_query_size(p, C, sigma, prec_arg, &sz));
+// Build the rows of g into SELL-C-sigma (sizes sz from query_sizes).
+cfd_status build_impl(const Lattice &g, const cfd_topi_params *p, int C, int sigma, int prec_arg,
+                      const cfd_matrix_sizes &sz, const cfd_matrix_buffers *buf, cfd_matrix *out,
+                      cudaStream_t stream) {
     const bool packed = (prec_arg & CFD_PACK_RI) != 0;
     const int prec = prec_arg & ~CFD_PACK_RI;
     if (!buf || !out) return fail(CFD_ERR_ARG, "buffers or out is NULL");
@@ -468,7 +484,6 @@ cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec
     if (!aligned16(buf->val) || !aligned16(buf->col) || !aligned16(buf->chunk_ptr) ||
         !aligned16(buf->chunk_len) || !aligned16(buf->work) || (buf->perm && !aligned16(buf->perm)))
         return fail(CFD_ERR_ARG, "matrix buffers must be 16-byte aligned");
-    Lattice g = lattice_of(p);
     TopiValues v{p->t, p->m, p->gamma, p->seed};
     int log2C = 0;
     while ((1 << log2C) < C) ++log2C;
@@ -515,13 +530,99 @@ cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec
     out->C = C;
     out->sigma = sigma;
     out->prec = prec;
-    out->flags = ((prec_arg & CFD_PACK_RI) ? CFD_MATRIX_PACKED : 0) | (TOPI_MAX_ROW << CFD_MATRIX_SLOTS_SHIFT);
+    out->flags = (packed ? CFD_MATRIX_PACKED : 0) | (TOPI_MAX_ROW << CFD_MATRIX_SLOTS_SHIFT);
     out->val = buf->val;
     out->col = static_cast<int32_t *>(buf->col);
     out->chunk_ptr = chunk_ptr;
     out->chunk_len = chunk_len;
     out->perm = perm;
     return CFD_OK;
+}
+
+}  // namespace
+}  // namespace cfd
+
+using namespace cfd;
+
+extern "C" {
+
+// ------------------------------------------------ z-slab distribution --
+
+cfd_status cfd_slab_plan(const cfd_topi_params *p, int nranks, int rank, cfd_slab *out) {
+    clear_error();
+    CFD_TRY(check_params(p, 32, 1, CFD_C128));
+    if (!out) return fail(CFD_ERR_ARG, "out is NULL");
+    if (nranks < 1 || rank < 0 || rank >= nranks) return fail(CFD_ERR_ARG, "rank %d of %d invalid", rank, nranks);
+    if (nranks > p->Nz) return fail(CFD_ERR_ARG, "%d ranks for %d z-planes: every rank needs a plane", nranks, p->Nz);
+    const int64_t plane = 4LL * p->Nx * p->Ny;
+    const int Nz = p->Nz;
+    cfd_slab s;
+    s.nranks = nranks;
+    s.rank = rank;
+    s.z0 = (int32_t)((int64_t)rank * Nz / nranks);
+    s.z1 = (int32_t)((int64_t)(rank + 1) * Nz / nranks);
+    s.row0 = plane * s.z0;
+    s.n_local = plane * (s.z1 - s.z0);
+    s.plane = plane;
+    s.lo_rank = s.hi_rank = -1;
+    s.lo_base = s.hi_base = -1;
+    if (nranks > 1) {
+        if (s.z0 > 0) { s.lo_rank = rank - 1; s.lo_base = plane * (s.z0 - 1); }
+        else if (p->periodic_z) { s.lo_rank = nranks - 1; s.lo_base = plane * (Nz - 1); }
+        if (s.z1 < Nz) { s.hi_rank = rank + 1; s.hi_base = plane * s.z1; }
+        else if (p->periodic_z) { s.hi_rank = 0; s.hi_base = 0; }
+    }
+    *out = s;
+    return CFD_OK;
+}
+
+int64_t cfd_slab_local_col(const cfd_slab *s, int64_t col) {
+    if (!s) return -1;
+    Lattice g;
+    g.n_rows = s->n_local;
+    g.row0 = s->row0;
+    g.slab = 1;
+    g.plane = s->plane;
+    g.lo_base = s->lo_base;
+    g.hi_base = s->hi_base;
+    return local_col(col, g);
+}
+
+cfd_status cfd_slab_query_size(const cfd_topi_params *p, const cfd_slab *slab, int C, int sigma, int prec_arg,
+                               cfd_matrix_sizes *out) {
+    clear_error();
+    const int prec = prec_arg & ~CFD_PACK_RI;
+    CFD_TRY(check_params(p, C, sigma, prec));
+    if (!slab || !out) return fail(CFD_ERR_ARG, "slab or out is NULL");
+    if (slab->n_local < 1 || slab->plane != 4LL * p->Nx * p->Ny || slab->row0 + slab->n_local > 4LL * p->Nx * p->Ny * p->Nz)
+        return fail(CFD_ERR_ARG, "slab does not fit the lattice (use cfd_slab_plan)");
+    query_sizes(lattice_of_slab(p, slab), C, sigma, prec_arg, out);
+    return CFD_OK;
+}
+
+cfd_status cfd_build_matrix_slab(const cfd_topi_params *p, const cfd_slab *slab, int C, int sigma, int prec_arg,
+                                 const cfd_matrix_buffers *buf, cfd_matrix *out, cudaStream_t stream) {
+    cfd_matrix_sizes sz;
+    CFD_TRY(cfd_slab_query_size(p, slab, C, sigma, prec_arg, &sz));
+    return build_impl(lattice_of_slab(p, slab), p, C, sigma, prec_arg, sz, buf, out, stream);
+}
+
+
+cfd_status cfd_matrix_query_size(const cfd_topi_params *p, int C, int sigma, int prec_arg,
+                                 cfd_matrix_sizes *out) {
+    clear_error();
+    const int prec = prec_arg & ~CFD_PACK_RI;
+    CFD_TRY(check_params(p, C, sigma, prec));
+    if (!out) return fail(CFD_ERR_ARG, "out is NULL");
+    query_sizes(lattice_of(p), C, sigma, prec_arg, out);
+    return CFD_OK;
+}
+
+cfd_status cfd_build_matrix(const cfd_topi_params *p, int C, int sigma, int prec_arg,
+                            const cfd_matrix_buffers *buf, cfd_matrix *out, cudaStream_t stream) {
+    cfd_matrix_sizes sz;
+    CFD_TRY(cfd_matrix_query_size(p, C, sigma, prec_arg, &sz));
+    return build_impl(lattice_of(p), p, C, sigma, prec_arg, sz, buf, out, stream);
 }
 
 cfd_status cfd_batch_query_size(const cfd_topi_params *p, int R, int C, int sigma, int prec_arg,
