@@ -107,14 +107,17 @@ def parse():
     ap.add_argument("--tte-workload", default=None, choices=sorted(workloads.ALL),
                     help="the workload whose time to eigenpairs is measured (default: the 128x128x64 one)")
     ap.add_argument("--mode", default="filter",
-                    choices=["filter", "iteration", "batch", "fusion", "host", "sweep", "tte", "peaks", "kernel"],
+                    choices=["filter", "iteration", "batch", "fusion", "host", "sweep", "tte", "peaks", "kernel",
+                             "dist"],
                     help="filter: n_b = 32 blocks of the 200x200x100 lattice at n_p = 100, plus time to "
                          "eigenpairs (default); iteration: the 64x64x32 ChebFD iteration (filter, SVQB, "
                          "Rayleigh-Ritz); batch: 64 uneven realisations, batched vs looped; fusion: fused step "
                          "vs separate SpMMV + BLAS-1 calls; host: search space in host memory vs in HBM, against "
                          "n_p; sweep: fused-filter throughput per configuration; tte: time to eigenpairs, fp64 "
                          "vs mixed policy, on --tte-workload; peaks: measured FMA rates of the fp64 and fp32 "
-                         "pipes; kernel: filter calls on one n_b block of the 64x64x32 lattice (profiling case)")
+                         "pipes; kernel: filter calls on one n_b block of the 64x64x32 lattice (profiling case); "
+                         "dist: the 200x200x100 lattice split into z-slabs, one per rank, halos over NCCL")
+    ap.add_argument("--dist-mode", type=int, default=0, help="dist mode: 0 vector (Algorithm 3), 1 pipelined (4)")
     ap.add_argument("--host-lattice", default="64x64x32", help="host mode: lattice Nx x Ny x Nz")
     ap.add_argument("--host-n-s", type=int, default=128, help="host mode: search space width")
     ap.add_argument("--host-n-ps", default="2,5,10,20,50,100", help="host mode: filter degrees (comma list)")
@@ -132,7 +135,7 @@ def parse():
     ap.add_argument("--storage", default="packed", choices=["packed", "complex"],
                     help="matrix values as real-or-imaginary scalars (exact for Topi) or complex pairs")
     a = ap.parse_args()
-    w = LARGE if a.mode == "filter" else WORKLOAD
+    w = LARGE if a.mode in ("filter", "dist") else WORKLOAD
     a.n_b = a.n_b or w.n_b
     a.n_p = a.n_p or w.n_p
     return a
@@ -1141,6 +1144,63 @@ def run_kernel(a):
                       "model_gbs": round(model.step_bytes(H.N, H.nnz, a.n_b, prec) / t / 1e9, 1)}))
 
 
+def run_dist(a):
+    """The filter distributed over z-slabs of the 200x200x100 lattice, one slab
+    per rank and GPU (Sect. 6), halo planes exchanged with NCCL
+    (cfd_filter_slab_nccl): --dist-mode 0 vector mode (Algorithm 3), 1
+    pipelined mode (Algorithm 4).  One step = one n_b block filtered with n_p
+    fused steps; strong scaling (the lattice is fixed).  Under torchrun rank 0
+    makes the NCCL id and torch.distributed hands it to the others."""
+    import torch
+    import torch.distributed as dist
+    from paper_1803_02156_gb300 import binding as b, inputs
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("gloo")
+    w = LARGE
+    n_b, n_p = a.n_b, a.n_p
+    uid = b.cfd_nccl_unique_id() if rank == 0 else None
+    if world > 1:
+        box = [uid]
+        dist.broadcast_object_list(box, src=0)
+        uid = box[0]
+    comm = b.cfd_nccl_comm_init(uid, world, rank)
+    p = b.topi_params(*w.lattice, t=w.t, m=w.m, gamma=w.gamma, seed=w.seed, periodic=w.periodic)
+    s = b.cfd_slab_plan(p, world, rank)
+    H = b.cfd_build_matrix_slab(p, s, w.sell_C, w.sell_sigma, "c128p")
+    X = inputs.gaussian_block_device(w.N, n_b, seed=w.x_seed)[s.row0:s.row0 + s.n_local].contiguous()
+    arith = 1 if a.arith == "dw" else 0
+    mode = a.dist_mode
+
+    def step():
+        b.cfd_filter_slab_nccl(s, H, BOUNDS[0], BOUNDS[1], -0.3, 0.3, n_p, X, n_b, comm, mode=mode, moments=True,
+                               arith=arith)
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    b.cfd_nccl_comm_destroy(comm)
+    if rank == 0:
+        byts = a.steps * n_p * model.step_bytes(w.N, w.nnz, n_b, "c128")
+        print(json.dumps({"metric": METRIC + " (distributed over z-slabs)", "value": round(byts / t / 1e9, 3),
+                          "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+                          "ms_per_step": round(1e3 * t / a.steps, 3), "higher_is_better": True, "scaling": "strong",
+                          "dtype": "f32x2" if arith else "c128", "data": "synthetic",
+                          "config": {"workload": w.name, "N": w.N, "n_b": n_b, "n_p": n_p,
+                                     "mode": "pipelined" if mode else "vector", "parallelism": "z-slabs x%d" % world}}))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_peaks(a):
     """Measured FMA rates of the fp64 and fp32 pipes (the library's probe)."""
     import torch
@@ -1173,6 +1233,8 @@ def main():
         run_peaks(a)
     elif a.mode == "kernel":
         run_kernel(a)
+    elif a.mode == "dist":
+        run_dist(a)
     elif a.mode == "iteration":
         run_iteration(a)
     else:

@@ -104,3 +104,29 @@ def test_filter_slabs_rejects_bad_plan(b):
         b.cfd_filter_slabs(slabs[::-1], Hs[::-1], -8.6, 8.6, -0.5, 0.5, 10, Xs[::-1], 16)
     with pytest.raises(b.CfdError):
         b.cfd_filter_slabs(slabs, Hs, -8.6, 8.6, -0.5, 0.5, 10, Xs, 16, mode=2)
+
+
+@pytest.mark.parametrize("mode,arith", [(0, 1), (1, 0)])
+def test_filter_slab_nccl_single_rank(b, mode, arith):
+    """The NCCL path with one rank (no halo partner; the moment all-reduce
+    still runs through NCCL) equals cfd_filter on the whole matrix bit for
+    bit, moments to rounding."""
+    import torch
+    p = b.topi_params(8, 8, 6)
+    H = b.cfd_build_matrix(p, 32, 1, "c128p")
+    X0 = torch.from_numpy(inputs.gaussian_block(H.N, 32, seed=4)).cuda()
+    ref = X0.clone()
+    mu_ref = b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 30, ref, 16, moments=True, arith=arith)
+    try:
+        uid = b.cfd_nccl_unique_id()
+    except b.CfdError as e:
+        pytest.skip("NCCL not loadable here: %s" % e)
+    comm = b.cfd_nccl_comm_init(uid, 1, 0)
+    s = b.cfd_slab_plan(p, 1, 0)
+    Hs = b.cfd_build_matrix_slab(p, s, 32, 1, "c128p")
+    X = X0.clone()
+    mu = b.cfd_filter_slab_nccl(s, Hs, -8.6, 8.6, -0.5, 0.5, 30, X, 16, comm, mode=mode, moments=True, arith=arith)
+    torch.cuda.synchronize()
+    b.cfd_nccl_comm_destroy(comm)
+    assert torch.equal(X, ref)
+    assert (torch.max(torch.abs(mu - mu_ref)) / torch.max(torch.abs(mu_ref))).item() < 1e-13
