@@ -121,6 +121,8 @@ def parse():
     ap.add_argument("--host-lattice", default="64x64x32", help="host mode: lattice Nx x Ny x Nz")
     ap.add_argument("--host-n-s", type=int, default=128, help="host mode: search space width")
     ap.add_argument("--host-n-ps", default="2,5,10,20,50,100", help="host mode: filter degrees (comma list)")
+    ap.add_argument("--host-layout", default="blocked", choices=["blocked", "rowmajor"],
+                    help="host mode: search space block after block (one contiguous copy per block) or row-major")
     ap.add_argument("--realisations", type=int, default=workloads.BATCH_COUNT)
     ap.add_argument("--prec", default="c128", choices=["c128", "c64"], help="filter arithmetic")
     ap.add_argument("--gather", type=int, default=0, help="kernel mode: cfd_filter_opts.gather")
@@ -971,7 +973,9 @@ def run_host(a):
     # page-locked by registering exactly the array's bytes (torch's pinned
     # allocator would round a 131 GB request up to a power of two)
     import numpy as np
-    Xn = np.empty((N, n_s), dtype=np.complex128)
+    blocked = a.host_layout == "blocked"
+    nblk = n_s // n_b
+    Xn = np.empty((nblk, N, n_b) if blocked else (N, n_s), dtype=np.complex128)
     rc = torch.cuda.cudart().cudaHostRegister(Xn.ctypes.data, Xn.nbytes, 0)
     if int(rc) != 0:
         raise RuntimeError("cudaHostRegister of %d bytes failed (%s)" % (Xn.nbytes, rc))
@@ -981,7 +985,11 @@ def run_host(a):
 
     def reset():
         inputs.fill_gaussian_device(dev, w.x_seed)
-        Xh.copy_(dev)
+        if blocked:
+            for k in range(nblk):
+                Xh[k].copy_(dev[:, k * n_b:(k + 1) * n_b])
+        else:
+            Xh.copy_(dev)
         torch.cuda.synchronize()
 
     def timed(f):
@@ -1001,9 +1009,15 @@ def run_host(a):
                                            b._stream(stream)))
 
         def run_host_():
-            b._check(b.lib().cfd_filter_host_ex(H.ref(), BOUNDS[0], BOUNDS[1], -0.3, 0.3, n_p, b.block_of(Xh), n_b,
-                                                b._ptr(work), work.numel(), b._ptr(None), b.ctypes.byref(o),
-                                                b._stream(stream)))
+            if blocked:
+                blk = b.cfd_block(Xh.data_ptr(), N, n_b, n_s, b.CFD_C128)
+                b._check(b.lib().cfd_filter_host_blocked(H.ref(), BOUNDS[0], BOUNDS[1], -0.3, 0.3, n_p, blk, n_b,
+                                                         b._ptr(work), work.numel(), b._ptr(None), b.ctypes.byref(o),
+                                                         b._stream(stream)))
+            else:
+                b._check(b.lib().cfd_filter_host_ex(H.ref(), BOUNDS[0], BOUNDS[1], -0.3, 0.3, n_p, b.block_of(Xh),
+                                                    n_b, b._ptr(work), work.numel(), b._ptr(None),
+                                                    b.ctypes.byref(o), b._stream(stream)))
         res = {"device": [], "host": []}
         for r in range(a.warmup + a.steps):
             reset()
@@ -1014,7 +1028,8 @@ def run_host(a):
                 res["host"].append(th)
         # the host filter's result equals the device filter's (sampled rows)
         idx = torch.linspace(0, N - 1, 4096, dtype=torch.int64)
-        same = bool(torch.equal(Xh[idx], dev[idx.cuda()].cpu()))
+        hrows = torch.cat([Xh[k][idx] for k in range(nblk)], dim=1) if blocked else Xh[idx]
+        same = bool(torch.equal(hrows, dev[idx.cuda()].cpu()))
         td, th = statistics.median(res["device"]), statistics.median(res["host"])
         moved = 2 * N * n_s * 16
         rows.append({"n_p": n_p, "device_s": round(td, 5), "host_s": round(th, 5),
@@ -1027,7 +1042,8 @@ def run_host(a):
                       "steps": a.steps, "warmup": a.warmup, "data": "synthetic", "dtype": "c128",
                       "arith": a.arith,
                       "config": {"workload": "topi-%s" % a.host_lattice, "N": N, "n_s": n_s, "n_b": n_b,
-                                 "host_bytes": N * n_s * 16, "storage": "packed", "pinned": True},
+                                 "host_bytes": N * n_s * 16, "storage": "packed", "pinned": True,
+                                 "host_layout": a.host_layout},
                       "results": rows}))
 
 

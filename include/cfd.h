@@ -346,6 +346,17 @@ cfd_status cfd_filter_host_ex(const cfd_matrix *H, double lmin, double lmax, dou
                               const cfd_filter_opts *opts, cudaStream_t stream);
 
 /*
+ * cfd_filter_host_ex for a search space stored block after block in host
+ * memory (block b of n_b columns, N rows of n_b complex values, at
+ * X.ptr + b N n_b scalars; X.n_rows = N, X.n_cols = n_s, X.ld = n_b): each
+ * block moves over the link as one contiguous copy.  Results equal
+ * cfd_filter's on the same columns bit for bit.
+ */
+cfd_status cfd_filter_host_blocked(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
+                                   int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,
+                                   const cfd_filter_opts *opts, cudaStream_t stream);
+
+/*
  * Chebyshev moments only (the kernel polynomial method: Algorithm 1 without
  * line 12, Sect. 2): for the columns of R (N x n_s, the matrix's precision,
  * not modified) mu[j][m] = <r_j, T_m(H~) r_j>, m = 0..2 n_p - 1, into

@@ -136,6 +136,10 @@ _PROTOS = {
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                           ctypes.POINTER(cfd_filter_opts), ctypes.c_void_p]),
+    "cfd_filter_host_blocked": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_int, cfd_block,
+                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                               ctypes.POINTER(cfd_filter_opts), ctypes.c_void_p]),
     "cfd_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cfd_kpm_moments": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        cfd_block, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
@@ -433,6 +437,28 @@ def cfd_filter_host(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, wor
     o = cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0)
     _check(lib().cfd_filter_host_ex(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
                                     _ptr(mu), ctypes.byref(o), _stream(stream)))
+    (stream or torch.cuda.current_stream()).synchronize()
+    return mu
+
+
+def cfd_filter_host_blocked(H, lmin, lmax, lam_l, lam_r, n_p, Xb, n_b, moments=False, work=None, stream=None,
+                            device="cuda", arith=0):
+    """The host-memory filter for a search space stored block after block: Xb
+    is a CPU tensor [n_s / n_b, N, n_b] (block b of n_b columns contiguous,
+    pinned for overlap), filtered in place (this call synchronises the
+    stream).  Returns the device moments when moments=True."""
+    if Xb.is_cuda or Xb.dim() != 3 or Xb.shape[2] != n_b or not Xb.is_contiguous():
+        raise ValueError("Xb must be a contiguous CPU tensor [n_s / n_b, N, n_b]")
+    prec = {torch.complex128: CFD_C128, torch.complex64: CFD_C64}[Xb.dtype]
+    nblk, N = Xb.shape[0], Xb.shape[1]
+    blk = cfd_block(Xb.data_ptr(), N, n_b, nblk * n_b, prec)
+    ws = cfd_filter_host_workspace(H.N, blk.n_cols, n_b, n_p, H.prec, blk.prec)
+    if work is None or work.numel() < ws:
+        work = _workspace(ws, device)
+    mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=device) if moments else None
+    o = cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0)
+    _check(lib().cfd_filter_host_blocked(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
+                                         _ptr(mu), ctypes.byref(o), _stream(stream)))
     (stream or torch.cuda.current_stream()).synchronize()
     return mu
 

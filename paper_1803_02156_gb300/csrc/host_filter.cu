@@ -98,11 +98,21 @@ extern "C" size_t cfd_filter_host_workspace(int64_t N, int n_s, int n_b, int n_p
     return host_filter_workspace(N, n_b, n_p, prec_H & 0xff, prec_X & 0xff);
 }
 
+// blocked: X holds the search space block after block (block b, rows of n_b
+// values, at X.ptr + b N n_b elements; X.ld == n_b), so a block moves as one
+// contiguous copy; else X is row-major with row stride X.ld.
 static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
                                    int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,
-                                   int arith, cudaStream_t stream) {
+                                   int arith, bool blocked, cudaStream_t stream) {
     CFD_TRY(check_matrix(H));
-    CFD_TRY(validate_block(X, H->n_rows));
+    if (blocked) {
+        if (X.ld != n_b) return fail(CFD_ERR_ARG, "a blocked search space has ld == n_b");
+        cfd_block one = X;
+        one.n_cols = n_b;
+        CFD_TRY(validate_block(one, H->n_rows));
+    } else {
+        CFD_TRY(validate_block(X, H->n_rows));
+    }
     if (n_b != 8 && n_b != 16 && n_b != 32 && n_b != 64) return fail(CFD_ERR_ARG, "n_b=%d not in {8,16,32,64}", n_b);
     if (X.n_cols % n_b) return fail(CFD_ERR_ARG, "n_b=%d does not divide n_s=%d", n_b, X.n_cols);
     if (n_p < 2) return fail(CFD_ERR_ARG, "n_p=%d < 2", n_p);
@@ -139,8 +149,12 @@ static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax
     // the copy stream starts after the work already queued on `stream`
     CFD_CUDA(cudaEventRecord(cp.start, stream));
     CFD_CUDA(cudaStreamWaitEvent(cp.copy, cp.start, 0));
+    const size_t block_bytes = (size_t)N * width;
     auto bring_in = [&](int b) -> cfd_status {
-        if (host_dev)
+        if (blocked)
+            CFD_CUDA(cudaMemcpyAsync(dbuf[b & 1], host + (size_t)b * block_bytes, block_bytes, cudaMemcpyHostToDevice,
+                                     cp.copy));
+        else if (host_dev)
             CFD_TRY(copy_rows(host_dev + (size_t)b * width, (int64_t)hpitch, dbuf[b & 1], (int64_t)width, N, width,
                               cp.copy));
         else
@@ -162,7 +176,10 @@ static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax
         CFD_CUDA(cudaEventRecord(cp.done[b & 1], stream));
         // write block b back, then reuse its buffer for block b + 2
         CFD_CUDA(cudaStreamWaitEvent(cp.copy, cp.done[b & 1], 0));
-        if (host_dev)
+        if (blocked)
+            CFD_CUDA(cudaMemcpyAsync(host + (size_t)b * block_bytes, dbuf[b & 1], block_bytes, cudaMemcpyDeviceToHost,
+                                     cp.copy));
+        else if (host_dev)
             CFD_TRY(copy_rows(dbuf[b & 1], (int64_t)width, host_dev + (size_t)b * width, (int64_t)hpitch, N, width,
                               cp.copy));
         else
@@ -180,7 +197,7 @@ extern "C" cfd_status cfd_filter_host(const cfd_matrix *H, double lmin, double l
                                       int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,
                                       cudaStream_t stream) {
     clear_error();
-    return filter_host_impl(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, work, work_bytes, moments, ARITH_NATIVE,
+    return filter_host_impl(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, work, work_bytes, moments, ARITH_NATIVE, false,
                             stream);
 }
 
@@ -192,5 +209,17 @@ extern "C" cfd_status cfd_filter_host_ex(const cfd_matrix *H, double lmin, doubl
                  opts->fixed_chunk || opts->graph))
         return fail(CFD_ERR_ARG, "cfd_filter_host_ex takes only the arith option");
     return filter_host_impl(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, work, work_bytes, moments,
-                            opts ? opts->arith : ARITH_NATIVE, stream);
+                            opts ? opts->arith : ARITH_NATIVE, false, stream);
+}
+
+extern "C" cfd_status cfd_filter_host_blocked(const cfd_matrix *H, double lmin, double lmax, double lam_l,
+                                              double lam_r, int n_p, cfd_block X, int n_b, void *work,
+                                              size_t work_bytes, double *moments, const cfd_filter_opts *opts,
+                                              cudaStream_t stream) {
+    clear_error();
+    if (opts && (opts->vpt || opts->grid_cap || opts->persistent || opts->staged || opts->gather ||
+                 opts->fixed_chunk || opts->graph))
+        return fail(CFD_ERR_ARG, "cfd_filter_host_blocked takes only the arith option");
+    return filter_host_impl(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, work, work_bytes, moments,
+                            opts ? opts->arith : ARITH_NATIVE, true, stream);
 }

@@ -59,6 +59,27 @@ def test_host_filter_vs_oracle(b, prec, tol):
     assert merr < tol, merr
 
 
+@pytest.mark.parametrize("prec,arith,pinned", [("c128p", 1, True), ("c128p", 0, False), ("c64p", 0, True)])
+def test_host_filter_blocked_equals_device_filter(b, prec, arith, pinned):
+    """A search space stored block after block in host memory (one contiguous
+    copy per block) gives the device filter's block and moments bit for bit."""
+    import torch
+    L, n_s, n_b, n_p = (12, 10, 7), 64, 16, 30
+    H = b.cfd_build_matrix(b.topi_params(*L, seed=1), 32, 1, prec)
+    dt = torch.complex64 if prec.startswith("c64") else torch.complex128
+    X = torch.from_numpy(inputs.gaussian_block(H.N, n_s, seed=2)).to(dt)
+    Xd = X.cuda()
+    mu_d = b.cfd_filter_ex(H, -8.6, 8.6, -0.6, 0.4, n_p, Xd, n_b, moments=True, arith=arith)
+    Xb = X.reshape(H.N, n_s // n_b, n_b).permute(1, 0, 2).contiguous()
+    if pinned:
+        Xb = Xb.pin_memory()
+    mu_h = b.cfd_filter_host_blocked(H, -8.6, 8.6, -0.6, 0.4, n_p, Xb, n_b, moments=True, arith=arith)
+    torch.cuda.synchronize()
+    got = Xb.permute(1, 0, 2).reshape(H.N, n_s)
+    assert torch.equal(got, Xd.cpu())
+    assert torch.equal(mu_h, mu_d)
+
+
 def test_host_filter_strided_host_block(b):
     """A column window of a wider host array (ld > n_s) is filtered in place;
     the other columns are untouched."""
