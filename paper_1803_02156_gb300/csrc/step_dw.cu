@@ -16,7 +16,9 @@
 //   * the result renormalised with TwoSum.
 // Each operation is accurate to a few units of 2^-48 relative to the sum of
 // the magnitudes of its terms (lo*lo products, below 2^-48 |hi*hi|, are
-// dropped), against 2^-53 for native fp64.
+// dropped), against 2^-53 for native fp64.  The real and imaginary parts of
+// an element go through the same sequence together, in Blackwell's packed
+// fp32x2 instructions (two lanes per issue slot).
 //
 // Storage stays 16 bytes per complex element: the recurrence blocks V_a, V_b
 // and, during one filter application, the caller's X block hold the
@@ -65,6 +67,53 @@ __device__ __forceinline__ void dw_axpy(float &xh, float &xl, float gh, float gl
 }
 
 __device__ __forceinline__ float4 ld_nc4(const float4 *p) { return __ldg(p); }
+
+// The same operations on two lanes at once with Blackwell's packed fp32x2
+// instructions (FADD2, FMUL2, FFMA2: one issue slot for two round-to-nearest
+// operations, each lane rounded exactly as the scalar instruction would).
+// The step is issue bound, and the real and imaginary parts of a complex
+// element run the same operation sequence, so pairing them halves the
+// floating-point instructions; every lane's arithmetic is the scalar
+// recipe's (dw_mac, two_sum, dw_axpy) bit for bit.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 bcast2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 swap2(float2 a) { return make_float2(a.y, a.x); }
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = __fadd2_rn(a, b);
+    const float2 bv = __fadd2_rn(s, neg2(a));
+    e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bv)))), __fadd2_rn(b, neg2(bv)));
+}
+
+// (s, e) += (hh + hl) (vh + vl) lanewise; nhh = -hh, nhl = -hl.  The product
+// error is carried negated (ne = p - hh vh, exact, then minus the cross
+// terms), which rounds to the negation of the scalar recipe's pe.
+__device__ __forceinline__ void dw_mac2(float2 &s, float2 &e, float2 hh, float2 nhh, float2 nhl, float2 vh,
+                                        float2 vl) {
+    const float2 p = __fmul2_rn(hh, vh);
+    float2 ne = __ffma2_rn(nhh, vh, p);
+    ne = __ffma2_rn(nhh, vl, ne);
+    ne = __ffma2_rn(nhl, vh, ne);
+    float2 t, err;
+    two_sum2(s, p, t, err);
+    s = t;
+    e = __fadd2_rn(e, __fadd2_rn(err, neg2(ne)));
+}
+
+// x + g v lanewise for double-words (xh, xl), g = (gh, gl) with ngh = -gh,
+// ngl = -gl, v = (vh, vl); renormalised as dw_axpy.
+__device__ __forceinline__ void dw_axpy2(float2 &xh, float2 &xl, float2 gh, float2 ngh, float2 ngl, float2 vh,
+                                         float2 vl) {
+    const float2 p = __fmul2_rn(gh, vh);
+    float2 ne = __ffma2_rn(ngh, vh, p);
+    ne = __ffma2_rn(ngh, vl, ne);
+    ne = __ffma2_rn(ngl, vh, ne);
+    float2 t, err;
+    two_sum2(xh, p, t, err);
+    const float2 lo = __fadd2_rn(xl, __fadd2_rn(err, neg2(ne)));
+    xh = __fadd2_rn(t, lo);
+    xl = __fadd2_rn(lo, neg2(__fadd2_rn(xh, neg2(t))));
+}
 
 }  // namespace
 
@@ -136,9 +185,9 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
     if (!A.chunk_rid && NW) set_weights(A.gc + w0);
     // 32-bit gather offsets (16-byte units) when the chunk height is compiled in
     const uint32_t ld16 = (uint32_t)A.ldin;
-    float uu_s[VPT], uu_e[VPT], wu_s[VPT], wu_e[VPT];
+    float2 uu_s2[VPT], uu_e2[VPT], wu_s2[VPT], wu_e2[VPT];     // per lane (real part, imaginary part)
 #pragma unroll
-    for (int q = 0; q < VPT; ++q) uu_s[q] = uu_e[q] = wu_s[q] = wu_e[q] = 0.f;
+    for (int q = 0; q < VPT; ++q) uu_s2[q] = uu_e2[q] = wu_s2[q] = wu_e2[q] = make_float2(0.f, 0.f);
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -184,16 +233,16 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
                 const int32_t *colp = col_s(b) + rr;
                 const float2 *valp = val_s(b) + rr;
                 // the row sum starts at -V_prev (general), -X (second) or 0:
-                // (s, e) per real and imaginary part
+                // (s, e), lane 0 the real part, lane 1 the imaginary part
                 float4 u[VPT], xo[VPT];
-                float rs[VPT], re[VPT], is[VPT], ie[VPT];
+                float2 s2[VPT], e2[VPT];
 #pragma unroll
                 for (int q = 0; q < VPT; ++q) {
                     float4 w0v = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (KIND == STEP_GENERAL) w0v = wout[i * A.ldw + j0 + q];
                     if (KIND == STEP_SECOND) w0v = xdw[i * A.ldx + j0 + q];
-                    rs[q] = -w0v.x; re[q] = -w0v.z;
-                    is[q] = -w0v.y; ie[q] = -w0v.w;
+                    s2[q] = make_float2(-w0v.x, -w0v.y);
+                    e2[q] = make_float2(-w0v.z, -w0v.w);
                 }
                 auto gather = [&](int kk, float4 (&v)[VPT]) {
                     const int cc = max(colp[kk << log2C], 0);          // padding: col -1, value 0
@@ -206,24 +255,27 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
                         for (int q = 0; q < VPT; ++q) v[q] = ld_nc4(vin + (int64_t)cc * A.ldin + j0 + q);
                     }
                 };
+                // real slot: (re, im) += h (v_re, v_im); imaginary slot, with
+                // the accumulator lanes swapped to (im, re) for the whole
+                // group: (im, re) += (h, -h) (v_re, v_im), i.e. i h v
                 auto madd = [&](int kk, bool imag, const float4 (&v)[VPT]) {
                     const float2 h = valp[kk << log2C];
+                    const float2 hh = make_float2(h.x, imag ? -h.x : h.x);
+                    const float2 nhh = neg2(hh);
+                    const float2 nhl = make_float2(-h.y, imag ? h.y : -h.y);
 #pragma unroll
-                    for (int q = 0; q < VPT; ++q) {
-                        if (imag) {            // i h v: (-h v_im, h v_re)
-                            dw_mac(rs[q], re[q], -h.x, -h.y, v[q].y, v[q].w);
-                            dw_mac(is[q], ie[q], h.x, h.y, v[q].x, v[q].z);
-                        } else {
-                            dw_mac(rs[q], re[q], h.x, h.y, v[q].x, v[q].z);
-                            dw_mac(is[q], ie[q], h.x, h.y, v[q].y, v[q].w);
-                        }
-                    }
+                    for (int q = 0; q < VPT; ++q)
+                        dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y), make_float2(v[q].z, v[q].w));
                 };
                 constexpr int U = CFD_DW_GROUP;
                 for (int g = 0; g < 2; ++g) {             // real group, then imaginary group
                     const bool imag = g == 1;
                     int kk = imag ? nre : 0;
                     const int k1 = imag ? len : nre;
+                    if (imag) {
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q) { s2[q] = swap2(s2[q]); e2[q] = swap2(e2[q]); }
+                    }
                     for (; kk + U <= k1; kk += U) {
                         float4 vv[U][VPT];
 #pragma unroll
@@ -236,6 +288,10 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
                         gather(kk, v);
                         madd(kk, imag, v);
                     }
+                    if (imag) {
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q) { s2[q] = swap2(s2[q]); e2[q] = swap2(e2[q]); }
+                    }
                 }
                 // the own row of vin (moments; V1 in the second step's X
                 // update) and X
@@ -247,36 +303,35 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
                 // the new vector = the renormalised sum; X update; moments
 #pragma unroll
                 for (int q = 0; q < VPT; ++q) {
-                    float4 wn;
-                    two_sum(rs[q], re[q], wn.x, wn.z);
-                    two_sum(is[q], ie[q], wn.y, wn.w);
+                    float2 nh, nl;
+                    two_sum2(s2[q], e2[q], nh, nl);
+                    float4 wn = make_float4(nh.x, nh.y, nl.x, nl.y);
                     if (KIND == STEP_FIRST) wn = dw_scale(wn, 0.5f);
                     wout[i * A.ldw + j0 + q] = wn;
+                    const float2 wh = make_float2(wn.x, wn.y), wl = make_float2(wn.z, wn.w);
+                    const float2 uh = make_float2(u[q].x, u[q].y), ul = make_float2(u[q].z, u[q].w);
                     if (KIND != STEP_FIRST) {
-                        float xrh = xo[q].x, xrl = xo[q].z, xih = xo[q].y, xil = xo[q].w;
+                        float2 xh = make_float2(xo[q].x, xo[q].y), xl = make_float2(xo[q].z, xo[q].w);
                         if (KIND == STEP_SECOND) {
                             // g0 X + g1 V1 + g2 V2 as (0 + g0 X) + g1 V1 + g2 V2
-                            float ar = 0.f, al = 0.f, bi = 0.f, bl = 0.f;
-                            dw_axpy(ar, al, gh[0], gl[0], xrh, xrl);
-                            dw_axpy(bi, bl, gh[0], gl[0], xih, xil);
-                            dw_axpy(ar, al, gh[1], gl[1], u[q].x, u[q].z);
-                            dw_axpy(bi, bl, gh[1], gl[1], u[q].y, u[q].w);
-                            xrh = ar; xrl = al; xih = bi; xil = bl;
+                            float2 ah = make_float2(0.f, 0.f), al = make_float2(0.f, 0.f);
+                            dw_axpy2(ah, al, bcast2(gh[0]), bcast2(-gh[0]), bcast2(-gl[0]), xh, xl);
+                            dw_axpy2(ah, al, bcast2(gh[1]), bcast2(-gh[1]), bcast2(-gl[1]), uh, ul);
+                            xh = ah;
+                            xl = al;
                         }
-                        dw_axpy(xrh, xrl, gh[NW - 1], gl[NW - 1], wn.x, wn.z);
-                        dw_axpy(xih, xil, gh[NW - 1], gl[NW - 1], wn.y, wn.w);
+                        dw_axpy2(xh, xl, bcast2(gh[NW - 1]), bcast2(-gh[NW - 1]), bcast2(-gl[NW - 1]), wh, wl);
                         if (LAST) {
                             double2 *xd = reinterpret_cast<double2 *>(xdw + i * A.ldx + j0 + q);
-                            *xd = make_double2((double)xrh + (double)xrl, (double)xih + (double)xil);
+                            *xd = make_double2((double)xh.x + (double)xl.x, (double)xh.y + (double)xl.y);
                         } else {
-                            xdw[i * A.ldx + j0 + q] = make_float4(xrh, xih, xrl, xil);
+                            xdw[i * A.ldx + j0 + q] = make_float4(xh.x, xh.y, xl.x, xl.y);
                         }
                     }
                     if (MOM) {
-                        dw_mac(uu_s[q], uu_e[q], u[q].x, u[q].z, u[q].x, u[q].z);
-                        dw_mac(uu_s[q], uu_e[q], u[q].y, u[q].w, u[q].y, u[q].w);
-                        dw_mac(wu_s[q], wu_e[q], wn.x, wn.z, u[q].x, u[q].z);
-                        dw_mac(wu_s[q], wu_e[q], wn.y, wn.w, u[q].y, u[q].w);
+                        // lanewise: (re^2, im^2) and (wn_re u_re, wn_im u_im)
+                        dw_mac2(uu_s2[q], uu_e2[q], uh, neg2(uh), neg2(ul), uh, ul);
+                        dw_mac2(wu_s2[q], wu_e2[q], wh, neg2(wh), neg2(wl), uh, ul);
                     }
                 }
             }
@@ -304,11 +359,18 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
     if (MOM) {
         // the threads' double-word sums (s + e) as Kahan-form accumulators
         // (value s - c) for the shared deterministic reduction
+        // after adding the two lanes: (s.x + e.x) + (s.y + e.y) = t + lo
         MomentAcc<float> uu[VPT], wu[VPT];
+        auto lanes = [](float2 s, float2 e, MomentAcc<float> &m) {
+            float t, err;
+            two_sum(s.x, s.y, t, err);
+            m.s = t;
+            m.c = -__fadd_rn(__fadd_rn(e.x, e.y), err);
+        };
 #pragma unroll
         for (int q = 0; q < VPT; ++q) {
-            uu[q].s = uu_s[q]; uu[q].c = -uu_e[q];
-            wu[q].s = wu_s[q]; wu[q].c = -wu_e[q];
+            lanes(uu_s2[q], uu_e2[q], uu[q]);
+            lanes(wu_s2[q], wu_e2[q], wu[q]);
         }
         reduce_moments<float, NB, VPT>(A.partial, A.ticket, A.dots, uu, wu);
     }
