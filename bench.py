@@ -128,6 +128,8 @@ def parse():
     ap.add_argument("--gather", type=int, default=0, help="kernel mode: cfd_filter_opts.gather")
     ap.add_argument("--vpt", type=int, default=0, help="kernel mode: vectors per thread (0: default)")
     ap.add_argument("--no-moments", action="store_true", help="kernel mode: filter without moments")
+    ap.add_argument("--footprint", type=int, default=0,
+                    help="cfd_filter_opts.footprint: 0 footprint-staged general steps where they apply, -1 never")
     ap.add_argument("--arith", default="dw", choices=["native", "dw"],
                     help="complex128 filter: double-word arithmetic on the fp32 pipe (cfd_filter_opts.arith = 1, "
                          "the default) or native fp64 arithmetic")
@@ -365,7 +367,11 @@ def run_filter(a):
     blocks = [b.block_of(X[:, k * n_b:(k + 1) * n_b]) for k in range(n_blocks)]
 
     dw = prec == "c128" and a.arith == "dw"
-    opts = b.cfd_filter_opts(0, 0, 0, 0, 0, 0, 1 if dw else 0, 0)
+    opts = b.cfd_filter_opts(0, 0, 0, 0, 0, 0, 1 if dw else 0, 0, a.footprint)
+    # the footprint-staged steps apply to complex-float and double-word filters
+    # of C = 32, sigma = 1 packed matrices at n_b = 32
+    fp_on = (a.footprint >= 0 and n_b == 32 and w.sell_C == 32 and w.sell_sigma == 1 and a.storage == "packed"
+             and (dw or prec == "c64"))
 
     def filt(blk, npp=n_p):
         b._check(L.cfd_filter_ex(H.ref(), lmin, lmax, lam_l, lam_r, npp, blk, n_b, b._ptr(work), work.numel(),
@@ -422,12 +428,13 @@ def run_filter(a):
     gbs_launch = step_bytes / t_launch / 1e9
     hbm, hbm_src = measured_hbm_gbs()
     if dw:
-        kname = "k_cheb_step_dw"
+        kname = "k_cheb_step_fp_dw" if fp_on else "k_cheb_step_dw"
         traffic, tsrc = profiled_traffic(kname, n_b, N)
         roof = {"bound": "hbm", "achieved": round(gbs_launch, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(gbs_launch / hbm, 4), "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": hbm_src,
-                "kernel": "k_cheb_step_dw<%d,%d,moments,chunk height 32>" % (n_b, 2 if n_b >= 16 else 1),
+                "kernel": ("k_cheb_step_fp<double-word,%d,2,moments,%d stages>" % (n_b, 2) if fp_on else
+                           "k_cheb_step_dw<%d,%d,moments,chunk height 32>" % (n_b, 2 if n_b >= 16 else 1)),
                 "algorithmic": "nnz (16 + 4) + 5 N n_b 16 bytes per launch",
                 "avg_launch_ms": round(1e3 * t_launch, 4)}
     elif prec == "c128":
@@ -446,11 +453,13 @@ def run_filter(a):
                 "avg_launch_ms": round(1e3 * t_launch, 4), "hbm_gbs": round(gbs_launch, 1),
                 "hbm_frac": round(gbs_launch / hbm, 4), "hbm_peak": hbm}
     else:
-        kname = "k_cheb_step_staged_c64"
+        kname = "k_cheb_step_fp_c64" if fp_on else "k_cheb_step_staged_c64"
         traffic, tsrc = profiled_traffic(kname, n_b, N)
         roof = {"bound": "hbm", "achieved": round(gbs_launch, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(gbs_launch / hbm, 4), "traffic": traffic, "traffic_source": tsrc,
-                "peak_source": hbm_src, "kernel": "k_cheb_step_staged<float,%d,2,moments,%s>" % (n_b, a.storage),
+                "peak_source": hbm_src,
+                "kernel": ("k_cheb_step_fp<complex float,%d,2,moments,3 stages>" % n_b if fp_on else
+                           "k_cheb_step_staged<float,%d,2,moments,%s>" % (n_b, a.storage)),
                 "algorithmic": "nnz (8 + 4) + 5 N n_b 8 bytes per launch",
                 "avg_launch_ms": round(1e3 * t_launch, 4)}
     roof["avg_launch_note"] = ("(median step - median n_p=3 call) / (n_p - 3), CUDA events on the launch stream; "
@@ -1147,14 +1156,14 @@ def run_kernel(a):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         b.cfd_filter_ex(H, *BOUNDS, -0.3, 0.3, a.n_p, X, a.n_b, moments=not a.no_moments, arith=1 if dw else 0,
-                        gather=a.gather, vpt=a.vpt)
+                        gather=a.gather, vpt=a.vpt, footprint=a.footprint)
         e1.record()
         torch.cuda.synchronize()
         if r >= a.warmup:
             ts.append(e0.elapsed_time(e1) / 1e3)
     t = statistics.median(ts) / a.n_p
     print(json.dumps({"metric": "filter call, ms per step", "unit": "ms", "workload": w.name, "prec": prec,
-                      "arith": "dw" if dw else "native", "gather": a.gather, "vpt": a.vpt,
+                      "arith": "dw" if dw else "native", "gather": a.gather, "vpt": a.vpt, "footprint": a.footprint,
                       "moments": not a.no_moments, "n_b": a.n_b, "n_p": a.n_p,
                       "ms_per_step": round(1e3 * t, 4),
                       "model_gbs": round(model.step_bytes(H.N, H.nnz, a.n_b, prec) / t / 1e9, 1)}))

@@ -291,6 +291,14 @@ typedef struct cfd_filter_opts {
                              bounds, window, options) on the same device replay the cached graph (up to 16
                              are kept).  Results are bit for bit those of graph 0.  The first call of each
                              argument set captures, so make it outside any capture of your own. */
+    int32_t footprint;    /* general steps of complex-float filters and double-word complex-double filters
+                             (packed values, C = 32, sigma = 1, n_b = 32, two vectors per thread, one
+                             realisation): 0 (default) stages each chunk's footprint, the rows of V_cur its
+                             slots read, by TMA bulk copies into shared memory before the chunk is computed
+                             (the row ranges are found once per call); -1 never (every slot's V_cur row is
+                             gathered from global memory); n > 0 as 0 with at most n footprint rows per
+                             chunk (chunks with more are gathered from global memory).  Results do not depend
+                             on it (filtered block bit for bit; moments to the order of their sums). */
 } cfd_filter_opts;
 
 /* cfd_filter with explicit kernel options (the autotuner's knobs besides n_b,

@@ -65,7 +65,8 @@ class cfd_block(ctypes.Structure):
 class cfd_filter_opts(ctypes.Structure):
     _fields_ = [("vpt", ctypes.c_int32), ("grid_cap", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("staged", ctypes.c_int32), ("gather", ctypes.c_int32),
-                ("fixed_chunk", ctypes.c_int32), ("arith", ctypes.c_int32), ("graph", ctypes.c_int32)]
+                ("fixed_chunk", ctypes.c_int32), ("arith", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("footprint", ctypes.c_int32)]
 
 
 class cfd_solve_params(ctypes.Structure):
@@ -382,19 +383,21 @@ def cfd_filter(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, moments=False, work=Non
 
 
 def cfd_filter_ex(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, vpt=0, grid_cap=0, moments=False, work=None,
-                  stream=None, persistent=0, staged=0, gather=0, fixed_chunk=0, arith=0, graph=0):
+                  stream=None, persistent=0, staged=0, gather=0, fixed_chunk=0, arith=0, graph=0, footprint=0):
     """cfd_filter with the kernel options (vectors per thread, CTA cap, persistent
     launch, TMA staging: 1 on, -1 off, 0 default; gathers in flight per row in
     staged steps: 16 all at once, 4 groups of four, 0 default; fixed_chunk -1:
     generic staged kernel instead of the one compiled for C = 32; arith 1:
     complex-double general steps in double-word arithmetic on the fp32 pipe;
-    graph 1: the call captured once as a CUDA graph and replayed)."""
+    graph 1: the call captured once as a CUDA graph and replayed; footprint
+    0: general steps stage each chunk's V_cur rows by TMA where they apply,
+    -1 never, n > 0 at most n rows per chunk)."""
     blk = block_of(X)
     ws = cfd_filter_workspace(H.N, blk.n_cols, n_b, n_p, H.prec, blk.prec)
     if work is None or work.numel() < ws:
         work = _workspace(ws, X.device)
     mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=X.device) if moments else None
-    o = cfd_filter_opts(vpt, grid_cap, persistent, staged, gather, fixed_chunk, arith, graph)
+    o = cfd_filter_opts(vpt, grid_cap, persistent, staged, gather, fixed_chunk, arith, graph, footprint)
     _check(lib().cfd_filter_ex(H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, _ptr(work), work.numel(),
                                _ptr(mu), ctypes.byref(o), _stream(stream)))
     return mu

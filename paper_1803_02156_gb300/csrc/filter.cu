@@ -275,6 +275,7 @@ size_t filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int pr
     c.take<double>((size_t)n_p * n_b * 2);                    // raw dots
     c.take<double>((size_t)STEP_MAX_GRID * 2 * n_b);       // CTA partials
     c.take<unsigned>(64);                                     // ticket
+    if (n_b == 32) c.take<char>(footprint_bytes(N));          // chunk footprints
     return round_up(c.off, 256);
 }
 
@@ -322,6 +323,15 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
         CFD_TRY(launch_prepare_values(H, P.alpha, P.beta, P.chunk_rid, P.rcoef, P.rcoef_ld, ws.prep, ws.prep_bytes,
                                       stream));
         A.prep_val = ws.prep;
+    }
+    // footprint-staged general steps (complex float, or double-word), with
+    // the chunks' footprints found once per call
+    FpView F;
+    if (P.footprint >= 0 && !P.persistent && P.staged >= 1 && !P.chunk_rid && ws.fp &&
+        (dw || std::is_same<T, float>::value)) {
+        int fmax = footprint_rows_cap(H, n_b, vpt, dw);
+        if (P.footprint > 0) fmax = std::min(fmax, P.footprint);
+        if (fmax > 0) CFD_TRY(launch_footprint(H, fmax, ws.fp, ws.fp_bytes, &F, stream));
     }
     C *va = static_cast<C *>(ws.va), *vb = static_cast<C *>(ws.vb);
     const int n_blocks = X.n_cols / n_b;
@@ -379,8 +389,17 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
                 A.vin = cur; A.ldin = n_b; A.w = prev; A.ldw = n_b; A.p = p;
                 A.dots = moments ? ws.raw + (int64_t)(p - 1) * 2 * n_b : nullptr;
                 if constexpr (std::is_same<T, double>::value) {
+                    if (dw && F.fmax > 0) {
+                        CFD_TRY(launch_step_fp_dw(A, F, n_b, vpt, p == n_p, P.grid_cap, stream));
+                        continue;
+                    }
                     if (dw) {
                         CFD_TRY(launch_step_dw(STEP_GENERAL, n_b, vpt, A, p == n_p, P.grid_cap, stream));
+                        continue;
+                    }
+                } else {
+                    if (F.fmax > 0) {
+                        CFD_TRY(launch_step_fp(A, F, n_b, vpt, P.grid_cap, stream));
                         continue;
                     }
                 }
@@ -424,6 +443,8 @@ static FilterScratch carve_filter(const cfd_matrix *H, const cfd_block &X, int n
     ws.raw = c.take<double>((size_t)n_p * n_b * 2);
     ws.partial = c.take<double>((size_t)STEP_MAX_GRID * 2 * n_b);
     ws.ticket = c.take<unsigned>(64);
+    ws.fp_bytes = n_b == 32 ? footprint_bytes(H->n_rows) : 0;
+    ws.fp = ws.fp_bytes ? c.take<char>(ws.fp_bytes) : nullptr;
     ws.grid_cap = STEP_MAX_GRID;
     return ws;
 }
@@ -431,7 +452,7 @@ static FilterScratch carve_filter(const cfd_matrix *H, const cfd_block &X, int n
 cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
                             const cfd_block &X, int n_b, int vpt, int grid_cap, int persistent, int staged,
                             void *work, size_t work_bytes, double *moments, cudaStream_t stream, int gather,
-                            int fixed_chunk, int arith, int graph) {
+                            int fixed_chunk, int arith, int graph, int footprint) {
     CFD_TRY(check_filter_args(H, n_p, X, n_b, vpt));
     if (arith != ARITH_NATIVE && arith != ARITH_DW) return fail(CFD_ERR_ARG, "arith=%d not in {0, 1}", arith);
     if (arith == ARITH_DW) {
@@ -460,6 +481,7 @@ cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, doubl
     P.gather = gather > 0 ? gather : default_gather(H->prec);
     P.fixed_chunk = fixed_chunk;
     P.arith = arith;
+    P.footprint = footprint;
     P.alpha = 2.0 / (lmax - lmin);
     P.beta = 0.5 * (lmax + lmin);
     auto enqueue = [&](cudaStream_t s) -> cfd_status {
@@ -477,7 +499,7 @@ cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, doubl
         double lmin, lmax, lam_l, lam_r;
         const void *work, *moments;
         size_t work_bytes;
-        int n_p, n_b, vpt, grid_cap, persistent, staged, gather, fixed_chunk, arith, kind;
+        int n_p, n_b, vpt, grid_cap, persistent, staged, gather, fixed_chunk, arith, footprint, kind;
     } key;
     std::memset(&key, 0, sizeof(key));
     key.H = *H;
@@ -485,7 +507,8 @@ cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, doubl
     key.lmin = lmin; key.lmax = lmax; key.lam_l = lam_l; key.lam_r = lam_r;
     key.work = work; key.moments = moments; key.work_bytes = work_bytes;
     key.n_p = n_p; key.n_b = n_b; key.vpt = P.vpt; key.grid_cap = P.grid_cap; key.persistent = persistent;
-    key.staged = P.staged; key.gather = P.gather; key.fixed_chunk = fixed_chunk; key.arith = arith; key.kind = 1;
+    key.staged = P.staged; key.gather = P.gather; key.fixed_chunk = fixed_chunk; key.arith = arith; key.footprint = footprint;
+    key.kind = 1;
     return run_as_graph(&key, sizeof(key), stream, enqueue);
 }
 
@@ -665,12 +688,14 @@ cfd_status cfd_filter_ex(const cfd_matrix *H, double lmin, double lmax, double l
     int fixed_chunk = opts ? opts->fixed_chunk : 0;
     int arith = opts ? opts->arith : 0;
     int graph = opts ? opts->graph : 0;
+    int footprint = opts ? opts->footprint : 0;
     if (cap < 0) return fail(CFD_ERR_ARG, "grid_cap < 0");
+    if (footprint < -1) return fail(CFD_ERR_ARG, "footprint=%d < -1", footprint);
     if (staged < -1 || staged > 2) return fail(CFD_ERR_ARG, "staged=%d not in -1..2", staged);
     if (gather != 0 && gather != 4 && gather != 8 && gather != STEP_GATHER_ALL)
         return fail(CFD_ERR_ARG, "gather=%d not in {0, 4, 8, %d}", gather, STEP_GATHER_ALL);
     return filter_impl_opts(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, vpt, cap, pers, staged, work, work_bytes,
-                            moments, stream, gather, fixed_chunk, arith, graph);
+                            moments, stream, gather, fixed_chunk, arith, graph, footprint);
 }
 
 cfd_status cfd_kpm_moments(const cfd_matrix *H, double lmin, double lmax, int n_p, cfd_block R, int n_b, void *work,

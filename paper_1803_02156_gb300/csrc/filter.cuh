@@ -121,6 +121,31 @@ cfd_status launch_prepare_values_dw(const cfd_matrix *H, double alpha, double be
                                     const double *rcoef, int64_t rcoef_ld, void *out, size_t out_bytes,
                                     cudaStream_t stream);
 
+// Per-call footprints of the SELL chunks for the footprint-staged general
+// steps (step_fp.cu): the rows of V_cur each chunk reads, as row ranges
+// staged by TMA into shared memory, and every slot's column as its row there.
+struct FpView {
+    const uint16_t *lcol = nullptr;   // per slot (H's SELL layout): the column's row in the staged footprint
+    const int4 *info = nullptr;       // per chunk {ranges (-1: chunk not staged), rows, row of the first own row, 0}
+    const int2 *rng = nullptr;        // per chunk, 16 ranges {first row, rows}
+    int fmax = 0;                     // footprint rows one stage holds (0: footprint steps off)
+};
+// Workspace bytes of the footprints of an N-row matrix.
+size_t footprint_bytes(int64_t N);
+// Footprint rows one stage of the footprint step holds for H at n_b / vpt
+// (complex float, or complex double in double-word arithmetic); 0 when the
+// step does not apply (it needs packed values, C = 32, sigma = 1, n_b = 32,
+// two vectors per thread).
+int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw);
+// Builds the footprints of H's chunks (at most fmax rows each) in buf.
+cfd_status launch_footprint(const cfd_matrix *H, int fmax, void *buf, size_t buf_bytes, FpView *out,
+                            cudaStream_t stream);
+// One general step with the footprints staged (complex float; complex double
+// in double-word arithmetic, last: X written back as complex double).
+cfd_status launch_step_fp(const StepArgs<float> &A, const FpView &F, int nb, int vpt, int grid_cap, cudaStream_t s);
+cfd_status launch_step_fp_dw(const StepArgs<double> &A, const FpView &F, int nb, int vpt, bool last, int grid_cap,
+                             cudaStream_t s);
+
 // Runs body(s) captured as a CUDA graph on a library stream and launches the
 // graph on `stream`; later calls with the same key bytes (on the same device)
 // replay the cached executable without capturing again (graph.cu).
@@ -138,6 +163,7 @@ struct FilterPlan {
     int gather = 0;
     int fixed_chunk = 0;
     int arith = ARITH_NATIVE;
+    int footprint = 0;                    // footprint steps: 0 where they apply, < 0 never, > 0 at most this many rows
     double alpha = 0, beta = 0;
     const int32_t *chunk_rid = nullptr;   // batch: chunk -> realisation
     const double *rcoef = nullptr;        // batch: per realisation {alpha, beta, weights}
@@ -153,6 +179,8 @@ struct FilterScratch {
     void *va, *vb, *xn;
     void *prep;             // prepared matrix values (2 alpha (H - beta)), prep_bytes long
     size_t prep_bytes;
+    void *fp;               // chunk footprints (n_b = 32 only), fp_bytes long
+    size_t fp_bytes;
     double *gc, *raw, *partial;
     unsigned *ticket;
     int grid_cap;
@@ -192,7 +220,7 @@ cfd_status launch_widen(const float2 *src, int64_t lds, double2 *dst, int64_t ld
 cfd_status filter_impl_opts(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r, int n_p,
                             const cfd_block &X, int n_b, int vpt, int grid_cap, int persistent, int staged,
                             void *work, size_t work_bytes, double *moments, cudaStream_t stream, int gather = 0,
-                            int fixed_chunk = 0, int arith = ARITH_NATIVE, int graph = 0);
+                            int fixed_chunk = 0, int arith = ARITH_NATIVE, int graph = 0, int footprint = 0);
 size_t batched_workspace(int64_t N, int R, int n_s, int n_b, int n_p, int prec_H, int prec_X);
 cfd_status kpm_impl(const cfd_matrix *H, double lmin, double lmax, int n_p, const cfd_block &R, int n_b,
                     void *work, size_t work_bytes, double *moments, cudaStream_t stream);

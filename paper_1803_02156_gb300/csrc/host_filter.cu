@@ -220,7 +220,7 @@ extern "C" cfd_status cfd_filter_host_ex(const cfd_matrix *H, double lmin, doubl
                                          double *moments, const cfd_filter_opts *opts, cudaStream_t stream) {
     clear_error();
     if (opts && (opts->vpt || opts->grid_cap || opts->persistent || opts->staged || opts->gather ||
-                 opts->fixed_chunk || opts->graph))
+                 opts->fixed_chunk || opts->graph || opts->footprint))
         return fail(CFD_ERR_ARG, "cfd_filter_host_ex takes only the arith option");
     return filter_host_impl(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, work, work_bytes, moments,
                             opts ? opts->arith : ARITH_NATIVE, false, stream);
@@ -232,7 +232,7 @@ extern "C" cfd_status cfd_filter_host_blocked(const cfd_matrix *H, double lmin, 
                                               cudaStream_t stream) {
     clear_error();
     if (opts && (opts->vpt || opts->grid_cap || opts->persistent || opts->staged || opts->gather ||
-                 opts->fixed_chunk || opts->graph))
+                 opts->fixed_chunk || opts->graph || opts->footprint))
         return fail(CFD_ERR_ARG, "cfd_filter_host_blocked takes only the arith option");
     return filter_host_impl(H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, work, work_bytes, moments,
                             opts ? opts->arith : ARITH_NATIVE, true, stream);

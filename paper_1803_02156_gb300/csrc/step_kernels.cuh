@@ -521,8 +521,8 @@ template <> struct MomentRed<float> {
 
 // Deterministic reduction of the threads' moment sums: warps (shuffles), the
 // CTA (shared memory, fixed order), then across CTAs by the last CTA to finish
-// (ticket counter), each in a fixed order.
-template <typename T, int NB, int VPT>
+// (ticket counter), each in a fixed order.  WARPS: the CTA's warps.
+template <typename T, int NB, int VPT, int WARPS = STEP_WARPS>
 __device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket, double *dots,
                                                MomentAcc<T> (&uu)[VPT], MomentAcc<T> (&wu)[VPT]) {
     using Op = MomentRed<T>;
@@ -532,7 +532,7 @@ __device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket
     const int warp = threadIdx.x >> 5;
     const int sub = lane / TPR;
     const int j0 = (lane % TPR) * VPT;
-    __shared__ R red[STEP_WARPS][NB][2];
+    __shared__ R red[WARPS][NB][2];
     __shared__ bool last_cta;
     R s_uu[VPT], s_wu[VPT];
 #pragma unroll
@@ -556,7 +556,7 @@ __device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket
     for (int e = threadIdx.x; e < 2 * NB; e += blockDim.x) {
         R s = Op::zero();
 #pragma unroll
-        for (int w = 0; w < STEP_WARPS; ++w) s = Op::add(s, red[w][e >> 1][e & 1]);
+        for (int w = 0; w < WARPS; ++w) s = Op::add(s, red[w][e >> 1][e & 1]);
         Op::store(partial + (int64_t)blockIdx.x * 2 * NB + e, s);
     }
     __threadfence();
@@ -565,7 +565,7 @@ __device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket
     __syncthreads();
     if (last_cta) {
         __threadfence();
-        for (int e = warp; e < 2 * NB; e += STEP_WARPS) {
+        for (int e = warp; e < 2 * NB; e += WARPS) {
             R s = Op::zero();
             for (int b = lane; b < (int)gridDim.x; b += 32) s = Op::add(s, Op::load(partial + (int64_t)b * 2 * NB + e));
 #pragma unroll
