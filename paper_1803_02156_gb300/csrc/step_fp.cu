@@ -33,9 +33,13 @@ constexpr int FP_RMAX = 16;     // row ranges of a staged footprint
 constexpr int FP_GAP = 4;       // rows two ranges may be apart and still be merged
 constexpr int FP_KEYS = 512;    // slots + own rows of a chunk the builder sorts
 constexpr int FP_C = 32;        // chunk height the footprint steps are built for
-constexpr int FP_THREADS = STEP_WARPS * 32;
 
 }  // namespace
+
+// One arrival on a shared-memory mbarrier (release semantics).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 
 // Offsets of one stage's parts in dynamic shared memory (bytes), the same on
 // host and device: slot rows (uint16), prepared values, the chunk's V_prev
@@ -219,32 +223,47 @@ __device__ __forceinline__ void st_elems(E *p, const E (&v)[VPT]) {
 // prepared values), with the moments' dots <V_cur, V_cur>, Re <W, V_cur>.
 // MODE FPM_C64: complex float; FPM_DW: complex double in double-word
 // arithmetic (LAST: X written back as complex double).  Needs a C = 32 matrix
-// with sigma = 1, packed values, V_cur and V_prev with row stride NB.  S
-// stages in flight; XST: the chunk's X rows are staged too (else loaded when
-// the row starts).  One CTA of FP_THREADS per SM, chunks grid-stride.
-// Bounded waits as in the other staged steps: a wait that expires records
-// CFD_ERR_TIMEOUT in *A.status and the CTA returns once every copy it issued
-// has landed (CFD_STATUS_DRAIN_EXPIRED as well if that wait expires too);
-// A.staged == 2 is the test of that path (every stage expects 16 bytes more
-// than are copied).
-template <int MODE, int NB, int VPT, bool MOM, bool LAST, int S, bool XST>
-__global__ void __launch_bounds__(FP_THREADS, 1)
+// with sigma = 1, packed values, V_cur and V_prev with row stride NB.
+//
+// One CTA per SM, chunks grid-stride, warp-specialised: warp W (the
+// producer) stages chunk after chunk into a ring of S stages (TMA bulk
+// copies completing on the stage's `full` mbarrier) and warps 0..W-1 (the
+// consumers) compute each chunk's rows from shared memory, each warp
+// releasing the stage through the stage's `empty` mbarrier when it is done
+// with it; the producer refills a stage once all W consumer warps released
+// it.  No CTA-wide barrier per chunk.  XST: the chunk's X rows are staged
+// too (else each row's X is loaded when the row starts).  In the
+// double-word step a thread's vectors are lane % TPR + q TPR, so the 16-byte
+// shared-memory loads of a half-warp are contiguous (no bank conflicts).
+// Bounded waits as in the other staged steps: a wait that expires stops the
+// CTA (every warp leaves its loop; a shared flag tells the others), the
+// producer waits for every copy it issued to land (also bounded) and records
+// CFD_ERR_TIMEOUT in *A.status (with CFD_STATUS_DRAIN_EXPIRED if that wait
+// expired too), and the CTA returns without its moments.  A.staged == 2 is
+// the test of that path (every stage expects 16 bytes more than are copied).
+template <int MODE, int NB, int VPT, bool MOM, bool LAST, int S, bool XST, int W>
+__global__ void __launch_bounds__((W + 1) * 32, 1)
 k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int slots_cap) {
     using E = typename FpTypes<MODE>::E;
     using V = typename FpTypes<MODE>::V;
     constexpr bool DW = MODE == FPM_DW;
+    constexpr bool STRIDED = DW;
     constexpr int TPR = NB / VPT;
     constexpr int RPW = 32 / TPR;
-    constexpr int ROWS_PASS = STEP_WARPS * RPW;
+    constexpr int ROWS_PASS = W * RPW;
     constexpr int RB = NB * (int)sizeof(E);
     static_assert(TPR >= 1 && TPR <= 32 && (32 % TPR) == 0, "bad thread split");
+    static_assert(!(STRIDED && XST), "staged X rows are read with the consecutive layout");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[S];
+    __shared__ __align__(8) uint64_t empty[S];
     __shared__ int4 s_info[S];
+    __shared__ int s_abort;
     const FpLayout L = fp_layout(slots_cap, (int)sizeof(V), RB, F.fmax, XST);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = lane / TPR;
-    const int j0 = (lane % TPR) * VPT;
+    const int jt = lane % TPR;
+    auto jq = [&](int q) { return STRIDED ? jt + q * TPR : jt * VPT + q; };
     const int64_t n_rows = A.H.n_rows;
     const int64_t n_chunks = (n_rows + FP_C - 1) / FP_C;
     const E *vin = reinterpret_cast<const E *>(A.vin);
@@ -254,6 +273,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
     const V *gval = reinterpret_cast<const V *>(A.prep_val);
     const uint32_t tx_extra = A.staged == 2 ? 16u : 0u;
     const long long limit = A.staged == 2 ? (1LL << 24) : (1LL << 32);
+    volatile int *abort_flag = &s_abort;
 
     // the step's weight g_p c_p: as a float, or as a double-word (gh, gl)
     const double gd = A.gc[A.p];
@@ -267,236 +287,286 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
 
     if (tid == 0) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], W);
+        }
+        s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-
-    // warp 0: stage chunk c into stage s (all lanes take part)
-    auto issue = [&](int64_t c, int s) {
-        unsigned char *st = smem_raw + (size_t)s * L.stage;
-        int cl = 0, nr = 0, tot = 0, own_off = 0;
-        long long base = 0;
-        if (lane == 0) {
-            cl = __ldg(A.H.chunk_len + c);
-            base = __ldg(A.H.chunk_ptr + c);
-            const int4 inf = __ldg(F.info + c);
-            nr = inf.x;
-            tot = inf.y;
-            own_off = inf.z;
-        }
-        cl = __shfl_sync(0xffffffffu, cl, 0);
-        nr = __shfl_sync(0xffffffffu, nr, 0);
-        tot = __shfl_sync(0xffffffffu, tot, 0);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        const uint32_t nslot = (uint32_t)((cl & 0xffff) + (cl >> 16)) * FP_C;
-        const int own = (int)(n_rows - c * FP_C < FP_C ? n_rows - c * FP_C : FP_C);
-        int2 g = make_int2(0, 0);
-        if (lane < nr) g = __ldg(F.rng + c * FP_RMAX + lane);
-        // each range's first row in the stage: exclusive prefix of the rows
-        int off = g.y;
-#pragma unroll
-        for (int d = 1; d < FP_RMAX; d <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, off, d);
-            if (lane >= d) off += t;
-        }
-        off -= g.y;
-        const uint32_t bytes = nslot * (uint32_t)sizeof(V) + (uint32_t)own * RB * (XST ? 2u : 1u) +
-                               (nr >= 0 ? nslot * 2u + (uint32_t)tot * RB : 0u) + tx_extra;
-        if (lane == 0) s_info[s] = make_int4(cl, nr, own_off, own);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (lane == 0) mbar_expect_tx(&full[s], bytes);
-        __syncwarp();
-        if (lane == 0 && nr >= 0 && nslot) tma_load_1d(st + L.lcol, F.lcol + base, nslot * 2u, &full[s]);
-        if (lane == 1 && nslot) tma_load_1d(st + L.val, gval + base, nslot * (uint32_t)sizeof(V), &full[s]);
-        if (lane == 2) tma_load_1d(st + L.prev, wout + c * FP_C * NB, (uint32_t)own * RB, &full[s]);
-        if (XST && lane < own) tma_load_1d(st + L.xs + lane * RB, xio + (c * FP_C + lane) * ldx, RB, &full[s]);
-        if (lane < nr)
-            tma_load_1d(st + L.rows + (uint32_t)off * RB, vin + (int64_t)g.x * NB, (uint32_t)g.y * RB, &full[s]);
+    const int64_t first = blockIdx.x, stride = gridDim.x;
+    int issued = 0;              // producer: chunks issued
+    bool drained_done = false;   // producer: stopped, its copies waited for and the status recorded
+    // producer lane 0, after the CTA stopped: wait for the copies of the last
+    // S issues (all issued ones, if fewer) and record the timeout
+    auto drain = [&]() {
+        const int j0 = issued > S ? issued - S : 0;
+        if (tx_extra)
+            for (int j = j0; j < issued; ++j) mbar_complete_tx(&full[j % S], tx_extra);
+        bool drained = true;
+        for (int j = j0; j < issued; ++j)
+            drained = mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1), 1LL << 32) && drained;
+        atomicOr(A.status, drained ? (int)CFD_ERR_TIMEOUT : (int)CFD_ERR_TIMEOUT | CFD_STATUS_DRAIN_EXPIRED);
     };
 
-    // the rows of one chunk from stage s; SM: V_cur rows from the staged
-    // footprint (else, for an unstaged chunk, gathered from global memory)
-    auto rows = [&](auto sm_tag, int64_t c, int s) {
-        constexpr bool SM = decltype(sm_tag)::value;
-        const int4 inf = s_info[s];
-        const int cl = inf.x, own_off = inf.z, own = inf.w;
-        const int nre = cl & 0xffff, len = nre + (cl >> 16);
-        const unsigned char *st = smem_raw + (size_t)s * L.stage;
-        const uint16_t *lc_s = reinterpret_cast<const uint16_t *>(st + L.lcol);
-        const V *val_s = reinterpret_cast<const V *>(st + L.val);
-        const E *prev_s = reinterpret_cast<const E *>(st + L.prev);
-        const E *x_s = reinterpret_cast<const E *>(st + L.xs);
-        const E *rows_s = reinterpret_cast<const E *>(st + L.rows);
-        const int64_t gbase = SM ? 0 : __ldg(A.H.chunk_ptr + c);
-        for (int rr = warp * RPW + sub; rr < own; rr += ROWS_PASS) {
-            const int64_t i = c * FP_C + rr;
-            auto vrow = [&](int kk, E (&v)[VPT]) {
-                if constexpr (SM) {
-                    ld_elems<E, VPT>(rows_s + (int)lc_s[kk * FP_C + rr] * NB + j0, v);
-                } else {
-                    const int cc = max(__ldg(A.H.col + gbase + kk * FP_C + rr), 0);   // padding: col -1, value 0
-                    ldg_elems<E, VPT>(vin + (int64_t)cc * NB + j0, v);
-                }
-            };
-            E wo[VPT], xo[VPT], u[VPT];
-            ld_elems<E, VPT>(prev_s + rr * NB + j0, wo);
-            if constexpr (XST) ld_elems<E, VPT>(x_s + rr * NB + j0, xo);
-            else ld_elems<E, VPT>(xio + i * ldx + j0, xo);
-            if constexpr (!DW) {
-                // complex float: the row sum starts at -V_prev; real slots
-                // add h v, imaginary slots i h v
-                float2 acc[VPT];
+    if (warp == W) {
+        // ------------------------------------------------------ producer --
+        auto issue = [&](int64_t c, int s) {
+            unsigned char *st = smem_raw + (size_t)s * L.stage;
+            int cl = 0, nr = 0, tot = 0, own_off = 0;
+            long long base = 0;
+            if (lane == 0) {
+                cl = __ldg(A.H.chunk_len + c);
+                base = __ldg(A.H.chunk_ptr + c);
+                const int4 inf = __ldg(F.info + c);
+                nr = inf.x;
+                tot = inf.y;
+                own_off = inf.z;
+            }
+            cl = __shfl_sync(0xffffffffu, cl, 0);
+            nr = __shfl_sync(0xffffffffu, nr, 0);
+            tot = __shfl_sync(0xffffffffu, tot, 0);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const uint32_t nslot = (uint32_t)((cl & 0xffff) + (cl >> 16)) * FP_C;
+            const int own = (int)(n_rows - c * FP_C < FP_C ? n_rows - c * FP_C : FP_C);
+            int2 g = make_int2(0, 0);
+            if (lane < nr) g = __ldg(F.rng + c * FP_RMAX + lane);
+            // each range's first row in the stage: exclusive prefix of the rows
+            int off = g.y;
 #pragma unroll
-                for (int q = 0; q < VPT; ++q) acc[q] = make_float2(-wo[q].x, -wo[q].y);
-#pragma unroll 4
-                for (int kk = 0; kk < nre; ++kk) {
-                    E v[VPT];
-                    vrow(kk, v);
-                    const float h = val_s[kk * FP_C + rr];
-#pragma unroll
-                    for (int q = 0; q < VPT; ++q) {
-                        acc[q].x = fmaf(h, v[q].x, acc[q].x);
-                        acc[q].y = fmaf(h, v[q].y, acc[q].y);
-                    }
+            for (int d = 1; d < FP_RMAX; d <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, off, d);
+                if (lane >= d) off += t;
+            }
+            off -= g.y;
+            const uint32_t bytes = nslot * (uint32_t)sizeof(V) + (uint32_t)own * RB * (XST ? 2u : 1u) +
+                                   (nr >= 0 ? nslot * 2u + (uint32_t)tot * RB : 0u) + tx_extra;
+            if (lane == 0) s_info[s] = make_int4(cl, nr, own_off, own);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (lane == 0) mbar_expect_tx(&full[s], bytes);
+            __syncwarp();
+            if (lane == 0 && nr >= 0 && nslot) tma_load_1d(st + L.lcol, F.lcol + base, nslot * 2u, &full[s]);
+            if (lane == 1 && nslot) tma_load_1d(st + L.val, gval + base, nslot * (uint32_t)sizeof(V), &full[s]);
+            if (lane == 2) tma_load_1d(st + L.prev, wout + c * FP_C * NB, (uint32_t)own * RB, &full[s]);
+            if (XST && lane < own) tma_load_1d(st + L.xs + lane * RB, xio + (c * FP_C + lane) * ldx, RB, &full[s]);
+            if (lane < nr)
+                tma_load_1d(st + L.rows + (uint32_t)off * RB, vin + (int64_t)g.x * NB, (uint32_t)g.y * RB, &full[s]);
+        };
+        bool failed = false;
+        for (int64_t c = first; c < n_chunks; c += stride, ++issued) {
+            const int s = issued % S;
+            if (issued >= S) {
+                const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)((issued / S - 1) & 1), limit);
+                if (__any_sync(0xffffffffu, !ok || *abort_flag)) {
+                    failed = true;
+                    break;
                 }
-#pragma unroll 4
-                for (int kk = nre; kk < len; ++kk) {
-                    E v[VPT];
-                    vrow(kk, v);
-                    const float h = val_s[kk * FP_C + rr];
+            }
+            issue(c, s);
+        }
+        if (failed && lane == 0) {
+            *abort_flag = 1;
+            drain();
+            drained_done = true;
+        }
+    } else {
+        // ----------------------------------------------------- consumers --
+        auto lds_row = [&](const E *rowp, E (&v)[VPT]) {     // shared memory, or plain global loads
+            if constexpr (STRIDED) {
 #pragma unroll
-                    for (int q = 0; q < VPT; ++q) {
-                        acc[q].x = fmaf(-h, v[q].y, acc[q].x);
-                        acc[q].y = fmaf(h, v[q].x, acc[q].y);
-                    }
-                }
-                E xn[VPT];
-#pragma unroll
-                for (int q = 0; q < VPT; ++q) {
-                    xn[q].x = fmaf(g0, acc[q].x, xo[q].x);
-                    xn[q].y = fmaf(g0, acc[q].y, xo[q].y);
-                }
-                st_elems<E, VPT>(wout + i * NB + j0, acc);
-                st_elems<E, VPT>(xio + i * ldx + j0, xn);
-                if (MOM) {
-                    if constexpr (SM) ld_elems<E, VPT>(rows_s + (own_off + rr) * NB + j0, u);
-                    else ldg_elems<E, VPT>(vin + i * NB + j0, u);
-#pragma unroll
-                    for (int q = 0; q < VPT; ++q) {
-                        uu[q].add2(u[q].x, u[q].x, u[q].y, u[q].y);
-                        wu[q].add2(acc[q].x, u[q].x, acc[q].y, u[q].y);
-                    }
-                }
+                for (int q = 0; q < VPT; ++q) v[q] = rowp[jq(q)];
             } else {
-                // double-word: (s, e) per lane (re, im), started at -V_prev;
-                // the imaginary group runs with the accumulator lanes swapped
-                float2 s2[VPT], e2[VPT];
+                ld_elems<E, VPT>(rowp + jt * VPT, v);
+            }
+        };
+        auto ldg_row = [&](const E *rowp, E (&v)[VPT]) {     // read-only global loads
+            if constexpr (STRIDED) {
 #pragma unroll
-                for (int q = 0; q < VPT; ++q) {
-                    s2[q] = make_float2(-wo[q].x, -wo[q].y);
-                    e2[q] = make_float2(-wo[q].z, -wo[q].w);
-                }
-#pragma unroll 2
-                for (int kk = 0; kk < nre; ++kk) {
-                    E v[VPT];
-                    vrow(kk, v);
-                    const float2 h = val_s[kk * FP_C + rr];
-                    const float2 hh = make_float2(h.x, h.x);
-                    const float2 nhh = neg2(hh);
-                    const float2 nhl = make_float2(-h.y, -h.y);
+                for (int q = 0; q < VPT; ++q) v[q] = __ldg(rowp + jq(q));
+            } else {
+                ldg_elems<E, VPT>(rowp + jt * VPT, v);
+            }
+        };
+        auto st_row = [&](E *rowp, const E (&v)[VPT]) {
+            if constexpr (STRIDED) {
 #pragma unroll
-                    for (int q = 0; q < VPT; ++q)
-                        dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y), make_float2(v[q].z, v[q].w));
-                }
-#pragma unroll
-                for (int q = 0; q < VPT; ++q) {
-                    s2[q] = swap2(s2[q]);
-                    e2[q] = swap2(e2[q]);
-                }
-#pragma unroll 2
-                for (int kk = nre; kk < len; ++kk) {
-                    E v[VPT];
-                    vrow(kk, v);
-                    const float2 h = val_s[kk * FP_C + rr];
-                    const float2 hh = make_float2(h.x, -h.x);
-                    const float2 nhh = neg2(hh);
-                    const float2 nhl = make_float2(-h.y, h.y);
-#pragma unroll
-                    for (int q = 0; q < VPT; ++q)
-                        dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y), make_float2(v[q].z, v[q].w));
-                }
-#pragma unroll
-                for (int q = 0; q < VPT; ++q) {
-                    s2[q] = swap2(s2[q]);
-                    e2[q] = swap2(e2[q]);
-                }
-                if (MOM) {
-                    if constexpr (SM) ld_elems<E, VPT>(rows_s + (own_off + rr) * NB + j0, u);
-                    else ldg_elems<E, VPT>(vin + i * NB + j0, u);
-                }
-                E wn[VPT];
-#pragma unroll
-                for (int q = 0; q < VPT; ++q) {
-                    float2 nh, nl;
-                    two_sum2(s2[q], e2[q], nh, nl);
-                    wn[q] = make_float4(nh.x, nh.y, nl.x, nl.y);
-                }
-                st_elems<E, VPT>(wout + i * NB + j0, wn);
-#pragma unroll
-                for (int q = 0; q < VPT; ++q) {
-                    const float2 wh = make_float2(wn[q].x, wn[q].y), wl = make_float2(wn[q].z, wn[q].w);
-                    float2 xh = make_float2(xo[q].x, xo[q].y), xl = make_float2(xo[q].z, xo[q].w);
-                    dw_axpy2(xh, xl, bcast2(gh), bcast2(-gh), bcast2(-gl), wh, wl);
-                    if (LAST) {
-                        double2 *xd = reinterpret_cast<double2 *>(xio + i * ldx + j0 + q);
-                        *xd = make_double2((double)xh.x + (double)xl.x, (double)xh.y + (double)xl.y);
+                for (int q = 0; q < VPT; ++q) rowp[jq(q)] = v[q];
+            } else {
+                st_elems<E, VPT>(rowp + jt * VPT, v);
+            }
+        };
+        // this warp's rows of one chunk from stage s; SM: V_cur rows from the
+        // staged footprint (else, for an unstaged chunk, from global memory)
+        auto rows = [&](auto sm_tag, int64_t c, int s) {
+            constexpr bool SM = decltype(sm_tag)::value;
+            const int4 inf = s_info[s];
+            const int cl = inf.x, own_off = inf.z, own = inf.w;
+            const int nre = cl & 0xffff, len = nre + (cl >> 16);
+            const unsigned char *st = smem_raw + (size_t)s * L.stage;
+            const uint16_t *lc_s = reinterpret_cast<const uint16_t *>(st + L.lcol);
+            const V *val_s = reinterpret_cast<const V *>(st + L.val);
+            const E *prev_s = reinterpret_cast<const E *>(st + L.prev);
+            const E *x_s = reinterpret_cast<const E *>(st + L.xs);
+            const E *rows_s = reinterpret_cast<const E *>(st + L.rows);
+            const int64_t gbase = SM ? 0 : __ldg(A.H.chunk_ptr + c);
+            for (int rr = warp * RPW + sub; rr < own; rr += ROWS_PASS) {
+                const int64_t i = c * FP_C + rr;
+                auto vrow = [&](int kk, E (&v)[VPT]) {
+                    if constexpr (SM) {
+                        lds_row(rows_s + (int)lc_s[kk * FP_C + rr] * NB, v);
                     } else {
-                        xio[i * ldx + j0 + q] = make_float4(xh.x, xh.y, xl.x, xl.y);
+                        const int cc = max(__ldg(A.H.col + gbase + kk * FP_C + rr), 0);   // padding: col -1, value 0
+                        ldg_row(vin + (int64_t)cc * NB, v);
+                    }
+                };
+                E wo[VPT], xo[VPT], u[VPT];
+                lds_row(prev_s + rr * NB, wo);
+                if constexpr (XST) lds_row(x_s + rr * NB, xo);
+                else lds_row(xio + i * ldx, xo);
+                if constexpr (!DW) {
+                    // complex float: the row sum starts at -V_prev; real slots
+                    // add h v, imaginary slots i h v
+                    E acc[VPT];
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) {
+                        acc[q].x = -wo[q].x;
+                        acc[q].y = -wo[q].y;
+                    }
+#pragma unroll 4
+                    for (int kk = 0; kk < nre; ++kk) {
+                        E v[VPT];
+                        vrow(kk, v);
+                        const float h = val_s[kk * FP_C + rr];
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q) {
+                            acc[q].x = fmaf(h, v[q].x, acc[q].x);
+                            acc[q].y = fmaf(h, v[q].y, acc[q].y);
+                        }
+                    }
+#pragma unroll 4
+                    for (int kk = nre; kk < len; ++kk) {
+                        E v[VPT];
+                        vrow(kk, v);
+                        const float h = val_s[kk * FP_C + rr];
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q) {
+                            acc[q].x = fmaf(-h, v[q].y, acc[q].x);
+                            acc[q].y = fmaf(h, v[q].x, acc[q].y);
+                        }
+                    }
+                    E xn[VPT];
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) {
+                        xn[q].x = fmaf(g0, acc[q].x, xo[q].x);
+                        xn[q].y = fmaf(g0, acc[q].y, xo[q].y);
+                    }
+                    st_row(wout + i * NB, acc);
+                    st_row(xio + i * ldx, xn);
+                    if (MOM) {
+                        if constexpr (SM) lds_row(rows_s + (own_off + rr) * NB, u);
+                        else ldg_row(vin + i * NB, u);
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q) {
+                            uu[q].add2(u[q].x, u[q].x, u[q].y, u[q].y);
+                            wu[q].add2(acc[q].x, u[q].x, acc[q].y, u[q].y);
+                        }
+                    }
+                } else {
+                    // double-word: (s, e) per lane (re, im), started at -V_prev;
+                    // the imaginary group runs with the accumulator lanes swapped
+                    float2 s2[VPT], e2[VPT];
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) {
+                        s2[q] = make_float2(-wo[q].x, -wo[q].y);
+                        e2[q] = make_float2(-wo[q].z, -wo[q].w);
+                    }
+#pragma unroll 2
+                    for (int kk = 0; kk < nre; ++kk) {
+                        E v[VPT];
+                        vrow(kk, v);
+                        const float2 h = val_s[kk * FP_C + rr];
+                        const float2 hh = make_float2(h.x, h.x);
+                        const float2 nhh = neg2(hh);
+                        const float2 nhl = make_float2(-h.y, -h.y);
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q)
+                            dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y),
+                                    make_float2(v[q].z, v[q].w));
+                    }
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) {
+                        s2[q] = swap2(s2[q]);
+                        e2[q] = swap2(e2[q]);
+                    }
+#pragma unroll 2
+                    for (int kk = nre; kk < len; ++kk) {
+                        E v[VPT];
+                        vrow(kk, v);
+                        const float2 h = val_s[kk * FP_C + rr];
+                        const float2 hh = make_float2(h.x, -h.x);
+                        const float2 nhh = neg2(hh);
+                        const float2 nhl = make_float2(-h.y, h.y);
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q)
+                            dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y),
+                                    make_float2(v[q].z, v[q].w));
+                    }
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) {
+                        s2[q] = swap2(s2[q]);
+                        e2[q] = swap2(e2[q]);
                     }
                     if (MOM) {
-                        const float2 uh = make_float2(u[q].x, u[q].y), ul = make_float2(u[q].z, u[q].w);
-                        dw_mac2(uu_s2[q], uu_e2[q], uh, neg2(uh), neg2(ul), uh, ul);
-                        dw_mac2(wu_s2[q], wu_e2[q], wh, neg2(wh), neg2(wl), uh, ul);
+                        if constexpr (SM) lds_row(rows_s + (own_off + rr) * NB, u);
+                        else ldg_row(vin + i * NB, u);
+                    }
+                    E wn[VPT];
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) {
+                        float2 nh, nl;
+                        two_sum2(s2[q], e2[q], nh, nl);
+                        wn[q] = make_float4(nh.x, nh.y, nl.x, nl.y);
+                    }
+                    st_row(wout + i * NB, wn);
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) {
+                        const float2 wh = make_float2(wn[q].x, wn[q].y), wl = make_float2(wn[q].z, wn[q].w);
+                        float2 xh = make_float2(xo[q].x, xo[q].y), xl = make_float2(xo[q].z, xo[q].w);
+                        dw_axpy2(xh, xl, bcast2(gh), bcast2(-gh), bcast2(-gl), wh, wl);
+                        if (LAST) {
+                            double2 *xd = reinterpret_cast<double2 *>(xio + i * ldx + jq(q));
+                            *xd = make_double2((double)xh.x + (double)xl.x, (double)xh.y + (double)xl.y);
+                        } else {
+                            xio[i * ldx + jq(q)] = make_float4(xh.x, xh.y, xl.x, xl.y);
+                        }
+                        if (MOM) {
+                            const float2 uh = make_float2(u[q].x, u[q].y), ul = make_float2(u[q].z, u[q].w);
+                            dw_mac2(uu_s2[q], uu_e2[q], uh, neg2(uh), neg2(ul), uh, ul);
+                            dw_mac2(wu_s2[q], wu_e2[q], wh, neg2(wh), neg2(wl), uh, ul);
+                        }
                     }
                 }
             }
-        }
-    };
-
-    const int64_t first = blockIdx.x, stride = gridDim.x;
-    if (warp == 0)
-        for (int s = 0; s < S; ++s)
-            if (first + (int64_t)s * stride < n_chunks) issue(first + (int64_t)s * stride, s);
-    bool ok = true;
-    int k = 0;
-    for (int64_t c = first; c < n_chunks; c += stride, ++k) {
-        const int s = k % S;
-        const bool landed = mbar_wait_bounded(&full[s], (uint32_t)((k / S) & 1), limit);
-        if (landed) {
+        };
+        int k = 0;
+        for (int64_t c = first; c < n_chunks; c += stride, ++k) {
+            if (__any_sync(0xffffffffu, *abort_flag)) break;
+            const int s = k % S;
+            const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / S) & 1), limit);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) *abort_flag = 1;
+                break;
+            }
             if (s_info[s].y >= 0) rows(std::integral_constant<bool, true>{}, c, s);
             else rows(std::integral_constant<bool, false>{}, c, s);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
         }
-        if (!__syncthreads_and(landed)) {
-            ok = false;
-            break;
-        }
-        const int64_t cn = c + (int64_t)S * stride;
-        if (warp == 0 && cn < n_chunks) issue(cn, s);
     }
-    if (!ok) {
-        if (tid == 0) {
-            // the copies issued and not consumed: iterations k .. k + S - 1
-            bool drained = true;
-            if (tx_extra)
-                for (int j = 0; j < S; ++j)
-                    if (first + (int64_t)(k + j) * stride < n_chunks) mbar_complete_tx(&full[(k + j) % S], tx_extra);
-            for (int j = 0; j < S; ++j)
-                if (first + (int64_t)(k + j) * stride < n_chunks)
-                    drained = mbar_wait_bounded(&full[(k + j) % S], (uint32_t)(((k + j) / S) & 1), 1LL << 32) &&
-                              drained;
-            atomicOr(A.status, drained ? (int)CFD_ERR_TIMEOUT : (int)CFD_ERR_TIMEOUT | CFD_STATUS_DRAIN_EXPIRED);
-        }
+    __syncthreads();
+    if (*abort_flag) {
+        if (warp == W && lane == 0 && !drained_done) drain();
         return;
     }
     if (MOM) {
@@ -514,7 +584,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                 lanes(wu_s2[q], wu_e2[q], wu[q]);
             }
         }
-        reduce_moments<float, NB, VPT>(A.partial, A.ticket, A.dots, uu, wu);
+        reduce_moments<float, NB, VPT, W + 1, STRIDED>(A.partial, A.ticket, A.dots, uu, wu);
     }
 }
 
@@ -531,6 +601,13 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
 #ifndef CFD_FP_DW_STAGES
 #define CFD_FP_DW_STAGES 2
 #endif
+// Consumer warps of the CTA (one CTA per SM, plus the producer warp).
+#ifndef CFD_FP_C64_WARPS
+#define CFD_FP_C64_WARPS 8
+#endif
+#ifndef CFD_FP_DW_WARPS
+#define CFD_FP_DW_WARPS 16
+#endif
 
 namespace {
 
@@ -540,10 +617,12 @@ template <int MODE> struct FpConf;
 template <> struct FpConf<FPM_C64> {
     static constexpr int S = CFD_FP_C64_STAGES;
     static constexpr bool XST = CFD_FP_C64_XST != 0;
+    static constexpr int W = CFD_FP_C64_WARPS;
 };
 template <> struct FpConf<FPM_DW> {
     static constexpr int S = CFD_FP_DW_STAGES;
     static constexpr bool XST = false;
+    static constexpr int W = CFD_FP_DW_WARPS;
 };
 
 // Dynamic shared memory a CTA may take next to the kernel's static shared
@@ -564,9 +643,10 @@ cfd_status fp_smem_budget(size_t *out) {
         CFD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         // the moments variant carries the reduction's static arrays
         cudaFuncAttributes fa{};
-        CFD_CUDA(cudaFuncGetAttributes(&fa, k_cheb_step_fp<MODE, FP_NB, FP_VPT, true, false, S, XST>));
+        constexpr int W = FpConf<MODE>::W;
+        CFD_CUDA(cudaFuncGetAttributes(&fa, k_cheb_step_fp<MODE, FP_NB, FP_VPT, true, false, S, XST, W>));
         cudaFuncAttributes fb{};
-        CFD_CUDA(cudaFuncGetAttributes(&fb, k_cheb_step_fp<MODE, FP_NB, FP_VPT, true, true, S, XST>));
+        CFD_CUDA(cudaFuncGetAttributes(&fb, k_cheb_step_fp<MODE, FP_NB, FP_VPT, true, true, S, XST, W>));
         const size_t stat = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
         cache[dev] = (size_t)optin > stat + 1024 ? (size_t)optin - stat - 1024 : 1;
     }
@@ -604,7 +684,8 @@ cfd_status launch_fp_t(const StepArgs<typename FpTypes<MODE>::T> &A, const FpVie
     size_t budget = 0;
     CFD_TRY(fp_smem_budget<MODE>(&budget));
     if (smem > budget) return fail(CFD_ERR_ARG, "footprint stages of %d rows need %zu bytes of shared memory", F.fmax, smem);
-    auto kern = k_cheb_step_fp<MODE, FP_NB, FP_VPT, MOM, LAST, S, XST>;
+    constexpr int W = FpConf<MODE>::W;
+    auto kern = k_cheb_step_fp<MODE, FP_NB, FP_VPT, MOM, LAST, S, XST, W>;
     struct Cache {
         std::mutex mu;
         int occ[64];
@@ -624,7 +705,7 @@ cfd_status launch_fp_t(const StepArgs<typename FpTypes<MODE>::T> &A, const FpVie
         }
         if (cache.occ[dev] == 0 || cache.occ_smem[dev] != smem) {
             int o = 0;
-            CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, FP_THREADS, smem));
+            CFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, (W + 1) * 32, smem));
             cache.occ[dev] = std::max(1, std::min(o, STEP_MAX_CTAS_PER_SM));
             cache.occ_smem[dev] = smem;
         }
@@ -634,7 +715,7 @@ cfd_status launch_fp_t(const StepArgs<typename FpTypes<MODE>::T> &A, const FpVie
     int64_t grid = std::min<int64_t>((int64_t)resident * sm_count(), n_chunks);
     if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
     grid = std::max<int64_t>(grid, 1);
-    kern<<<(unsigned)grid, FP_THREADS, smem, stream>>>(A, F, slots_cap);
+    kern<<<(unsigned)grid, (W + 1) * 32, smem, stream>>>(A, F, slots_cap);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;

@@ -521,8 +521,10 @@ template <> struct MomentRed<float> {
 
 // Deterministic reduction of the threads' moment sums: warps (shuffles), the
 // CTA (shared memory, fixed order), then across CTAs by the last CTA to finish
-// (ticket counter), each in a fixed order.  WARPS: the CTA's warps.
-template <typename T, int NB, int VPT, int WARPS = STEP_WARPS>
+// (ticket counter), each in a fixed order.  WARPS: the CTA's warps.  A
+// thread's vectors are (lane % TPR) VPT + q, or with STRIDED (lane % TPR) +
+// q TPR, q < VPT.
+template <typename T, int NB, int VPT, int WARPS = STEP_WARPS, bool STRIDED = false>
 __device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket, double *dots,
                                                MomentAcc<T> (&uu)[VPT], MomentAcc<T> (&wu)[VPT]) {
     using Op = MomentRed<T>;
@@ -531,7 +533,8 @@ __device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int sub = lane / TPR;
-    const int j0 = (lane % TPR) * VPT;
+    const int jt = lane % TPR;
+    auto jq = [&](int q) { return STRIDED ? jt + q * TPR : jt * VPT + q; };
     __shared__ R red[WARPS][NB][2];
     __shared__ bool last_cta;
     R s_uu[VPT], s_wu[VPT];
@@ -548,8 +551,8 @@ __device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket
     if (sub == 0) {
 #pragma unroll
         for (int q = 0; q < VPT; ++q) {
-            red[warp][j0 + q][0] = s_uu[q];
-            red[warp][j0 + q][1] = s_wu[q];
+            red[warp][jq(q)][0] = s_uu[q];
+            red[warp][jq(q)][1] = s_wu[q];
         }
     }
     __syncthreads();
