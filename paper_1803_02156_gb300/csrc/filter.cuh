@@ -126,8 +126,8 @@ cfd_status launch_prepare_values_dw(const cfd_matrix *H, double alpha, double be
 // staged by TMA into shared memory, and every slot's column as its row there.
 struct FpView {
     const uint16_t *lcol = nullptr;   // per slot (H's SELL layout): the column's row in the staged footprint
-    const int4 *info = nullptr;       // per chunk {ranges (-1: chunk not staged), rows, row of the first own row, 0}
-    const int2 *rng = nullptr;        // per chunk, 16 ranges {first row, rows}
+    const int2 *desc = nullptr;       // per chunk 32 words: {chunk_len, ranges (-1: not staged)}, {rows, row of
+                                      // the first own row}, first slot, 5 unused, 16 ranges {first row, rows}, 8 unused
     int fmax = 0;                     // footprint rows one stage holds (0: footprint steps off)
 };
 // Workspace bytes of the footprints of an N-row matrix.

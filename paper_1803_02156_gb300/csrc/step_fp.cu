@@ -66,12 +66,14 @@ __host__ __device__ inline FpLayout fp_layout(int slots_cap, int val_bytes, int 
 // One CTA per chunk (grid-stride): the chunk's slot columns and own rows are
 // sorted (bitonic, FP_KEYS keys, padding slots and unused keys INT_MAX),
 // runs of keys no more than FP_GAP apart become ranges, and each slot's
-// column is replaced by its row in the concatenated ranges.  info[c] =
-// {ranges (-1: not staged), footprint rows, row of the chunk's first own row,
-// 0}; rng[c FP_RMAX + r] = {first row, rows} of range r.
+// column is replaced by its row in the concatenated ranges.  The chunk's
+// descriptor desc[c 32 + l] (32 int2, one coalesced 256-byte load for a
+// warp) holds in word 0 {chunk_len, ranges (-1: not staged)}, word 1
+// {footprint rows, row of the chunk's first own row}, word 2 the chunk's
+// first slot (low, high 32 bits), words 8 + r {first row, rows} of range r.
 __global__ void __launch_bounds__(256) k_footprint(const int32_t *col, const int64_t *chunk_ptr,
                                                    const int32_t *chunk_len, int64_t n_rows, int64_t n_chunks,
-                                                   int fmax, uint16_t *lcol, int4 *info, int2 *rng) {
+                                                   int fmax, uint16_t *lcol, int2 *desc) {
     __shared__ int key[FP_KEYS];
     __shared__ int rs[FP_RMAX], re[FP_RMAX], ro[FP_RMAX];
     __shared__ int s_nr, s_total;
@@ -151,13 +153,18 @@ __global__ void __launch_bounds__(256) k_footprint(const int32_t *col, const int
             }
             return ro[lo] + (cc - rs[lo]);
         };
-        if (tid < FP_RMAX)
-            rng[c * FP_RMAX + tid] = tid < nr ? make_int2(rs[tid], re[tid] - rs[tid]) : make_int2(0, 0);
+        if (tid < 32) {
+            int2 d = make_int2(0, 0);
+            if (tid == 0) d = make_int2(cl, nr);
+            else if (tid == 1) d = make_int2(s_total, nr >= 0 ? local((int)r0) : 0);
+            else if (tid == 2) d = make_int2((int)(uint32_t)base, (int)(uint32_t)((uint64_t)base >> 32));
+            else if (tid >= 8 && tid - 8 < nr) d = make_int2(rs[tid - 8], re[tid - 8] - rs[tid - 8]);
+            desc[c * 32 + tid] = d;
+        }
         for (int t = tid; t < nslot; t += blockDim.x) {
             const int cc = col[base + t];
             lcol[base + t] = (uint16_t)((nr >= 0 && cc >= 0) ? local(cc) : 0);
         }
-        if (tid == 0) info[c] = make_int4(nr, s_total, nr >= 0 ? local((int)r0) : 0, 0);
         __syncthreads();
     }
 }
@@ -312,26 +319,21 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
 
     if (warp == W) {
         // ------------------------------------------------------ producer --
-        auto issue = [&](int64_t c, int s) {
+        // chunk c into stage s from its descriptor (lane l holds word l)
+        auto issue = [&](int64_t c, int s, int2 d) {
             unsigned char *st = smem_raw + (size_t)s * L.stage;
-            int cl = 0, nr = 0, tot = 0, own_off = 0;
-            long long base = 0;
-            if (lane == 0) {
-                cl = __ldg(A.H.chunk_len + c);
-                base = __ldg(A.H.chunk_ptr + c);
-                const int4 inf = __ldg(F.info + c);
-                nr = inf.x;
-                tot = inf.y;
-                own_off = inf.z;
-            }
-            cl = __shfl_sync(0xffffffffu, cl, 0);
-            nr = __shfl_sync(0xffffffffu, nr, 0);
-            tot = __shfl_sync(0xffffffffu, tot, 0);
-            base = __shfl_sync(0xffffffffu, base, 0);
+            const int cl = __shfl_sync(0xffffffffu, d.x, 0);
+            const int nr = __shfl_sync(0xffffffffu, d.y, 0);
+            const int tot = __shfl_sync(0xffffffffu, d.x, 1);
+            const int own_off = __shfl_sync(0xffffffffu, d.y, 1);
+            const long long base = (long long)(((uint64_t)(uint32_t)__shfl_sync(0xffffffffu, d.y, 2) << 32) |
+                                               (uint32_t)__shfl_sync(0xffffffffu, d.x, 2));
             const uint32_t nslot = (uint32_t)((cl & 0xffff) + (cl >> 16)) * FP_C;
             const int own = (int)(n_rows - c * FP_C < FP_C ? n_rows - c * FP_C : FP_C);
-            int2 g = make_int2(0, 0);
-            if (lane < nr) g = __ldg(F.rng + c * FP_RMAX + lane);
+            int2 g;
+            g.x = __shfl_sync(0xffffffffu, d.x, 8 + (lane & (FP_RMAX - 1)));
+            g.y = __shfl_sync(0xffffffffu, d.y, 8 + (lane & (FP_RMAX - 1)));
+            if (lane >= nr) g = make_int2(0, 0);
             // each range's first row in the stage: exclusive prefix of the rows
             int off = g.y;
 #pragma unroll
@@ -354,7 +356,11 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                 tma_load_1d(st + L.rows + (uint32_t)off * RB, vin + (int64_t)g.x * NB, (uint32_t)g.y * RB, &full[s]);
         };
         bool failed = false;
+        // descriptors one chunk ahead, so their load latency is off the issue path
+        int2 dnext = first < n_chunks ? __ldg(F.desc + first * 32 + lane) : make_int2(0, 0);
         for (int64_t c = first; c < n_chunks; c += stride, ++issued) {
+            const int2 d = dnext;
+            if (c + stride < n_chunks) dnext = __ldg(F.desc + (c + stride) * 32 + lane);
             const int s = issued % S;
             if (issued >= S) {
                 const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)((issued / S - 1) & 1), limit);
@@ -363,7 +369,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                     break;
                 }
             }
-            issue(c, s);
+            issue(c, s, d);
         }
         if (failed && lane == 0) {
             *abort_flag = 1;
@@ -398,7 +404,13 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
         };
         // this warp's rows of one chunk from stage s; SM: V_cur rows from the
         // staged footprint (else, for an unstaged chunk, from global memory)
-        auto rows = [&](auto sm_tag, int64_t c, int s) {
+        // one row per thread and chunk, X not staged: each thread loads its X
+        // row of the next chunk while it computes this one
+        constexpr bool XPRE = !XST && ROWS_PASS == FP_C;
+        const int my_rr = warp * RPW + sub;
+        auto x_row_exists = [&](int64_t c) { return c < n_chunks && c * FP_C + my_rr < n_rows; };
+        E xpre[VPT];
+        auto rows = [&](auto sm_tag, int64_t c, int s, const E (&xin)[VPT]) {
             constexpr bool SM = decltype(sm_tag)::value;
             const int4 inf = s_info[s];
             const int cl = inf.x, own_off = inf.z, own = inf.w;
@@ -408,6 +420,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
             const V *val_s = reinterpret_cast<const V *>(st + L.val);
             const E *prev_s = reinterpret_cast<const E *>(st + L.prev);
             const E *x_s = reinterpret_cast<const E *>(st + L.xs);
+            (void)x_s;
             const E *rows_s = reinterpret_cast<const E *>(st + L.rows);
             const int64_t gbase = SM ? 0 : __ldg(A.H.chunk_ptr + c);
             for (int rr = warp * RPW + sub; rr < own; rr += ROWS_PASS) {
@@ -422,8 +435,14 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                 };
                 E wo[VPT], xo[VPT], u[VPT];
                 lds_row(prev_s + rr * NB, wo);
-                if constexpr (XST) lds_row(x_s + rr * NB, xo);
-                else lds_row(xio + i * ldx, xo);
+                if constexpr (XST) {
+                    lds_row(x_s + rr * NB, xo);
+                } else if constexpr (XPRE) {
+#pragma unroll
+                    for (int q = 0; q < VPT; ++q) xo[q] = xin[q];
+                } else {
+                    lds_row(xio + i * ldx, xo);
+                }
                 if constexpr (!DW) {
                     // complex float: the row sum starts at -V_prev; real slots
                     // add h v, imaginary slots i h v
@@ -549,17 +568,22 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                 }
             }
         };
+        if (XPRE && x_row_exists(first)) lds_row(xio + (first * FP_C + my_rr) * ldx, xpre);
         int k = 0;
         for (int64_t c = first; c < n_chunks; c += stride, ++k) {
             if (__any_sync(0xffffffffu, *abort_flag)) break;
             const int s = k % S;
+            E xcur[VPT];
+#pragma unroll
+            for (int q = 0; q < VPT; ++q) xcur[q] = xpre[q];
+            if (XPRE && x_row_exists(c + stride)) lds_row(xio + ((c + stride) * FP_C + my_rr) * ldx, xpre);
             const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / S) & 1), limit);
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0) *abort_flag = 1;
                 break;
             }
-            if (s_info[s].y >= 0) rows(std::integral_constant<bool, true>{}, c, s);
-            else rows(std::integral_constant<bool, false>{}, c, s);
+            if (s_info[s].y >= 0) rows(std::integral_constant<bool, true>{}, c, s, xcur);
+            else rows(std::integral_constant<bool, false>{}, c, s, xcur);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
@@ -593,17 +617,17 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
 // Stages in flight and whether X rows are staged, per mode: the tuned
 // values, fixed at compile time.
 #ifndef CFD_FP_C64_STAGES
-#define CFD_FP_C64_STAGES 3
+#define CFD_FP_C64_STAGES 4
 #endif
 #ifndef CFD_FP_C64_XST
-#define CFD_FP_C64_XST 1
+#define CFD_FP_C64_XST 0
 #endif
 #ifndef CFD_FP_DW_STAGES
 #define CFD_FP_DW_STAGES 2
 #endif
 // Consumer warps of the CTA (one CTA per SM, plus the producer warp).
 #ifndef CFD_FP_C64_WARPS
-#define CFD_FP_C64_WARPS 8
+#define CFD_FP_C64_WARPS 16
 #endif
 #ifndef CFD_FP_DW_WARPS
 #define CFD_FP_DW_WARPS 16
@@ -736,8 +760,7 @@ cfd_status fp_check(const StepArgs<T> &A, const FpView &F, int nb, int vpt) {
 
 size_t footprint_bytes(int64_t N) {
     const int64_t n_chunks = (N + FP_C - 1) / FP_C;
-    return round_up((size_t)kMaxRowSlots * (size_t)(N + 127) * 2, 256) + round_up((size_t)n_chunks * 16, 256) +
-           round_up((size_t)n_chunks * FP_RMAX * 8, 256);
+    return round_up((size_t)kMaxRowSlots * (size_t)(N + 127) * 2, 256) + round_up((size_t)n_chunks * 256, 256);
 }
 
 int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw) {
@@ -758,16 +781,13 @@ cfd_status launch_footprint(const cfd_matrix *H, int fmax, void *buf, size_t buf
         return fail(CFD_ERR_INTERNAL, "footprint buffer too small");
     Carve c(buf, buf_bytes);
     uint16_t *lcol = c.take<uint16_t>((size_t)kMaxRowSlots * (size_t)(H->n_rows + 127));
-    int4 *info = c.take<int4>((size_t)n_chunks);
-    int2 *rng = c.take<int2>((size_t)n_chunks * FP_RMAX);
+    int2 *desc = c.take<int2>((size_t)n_chunks * 32);
     const int grid = (int)std::min<int64_t>(n_chunks, (int64_t)sm_count() * 8);
-    k_footprint<<<grid, 256, 0, stream>>>(H->col, H->chunk_ptr, H->chunk_len, H->n_rows, n_chunks, fmax, lcol, info,
-                                          rng);
+    k_footprint<<<grid, 256, 0, stream>>>(H->col, H->chunk_ptr, H->chunk_len, H->n_rows, n_chunks, fmax, lcol, desc);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     out->lcol = lcol;
-    out->info = info;
-    out->rng = rng;
+    out->desc = desc;
     out->fmax = fmax;
     return CFD_OK;
 }
