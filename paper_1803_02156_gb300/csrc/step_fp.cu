@@ -33,6 +33,20 @@ constexpr int FP_RMAX = 16;     // row ranges of a staged footprint
 constexpr int FP_GAP = 4;       // rows two ranges may be apart and still be merged
 constexpr int FP_KEYS = 512;    // slots + own rows of a chunk the builder sorts
 constexpr int FP_C = 32;        // chunk height the footprint steps are built for
+// Slots of a chunk whose rows all have six neighbours (Topi, packed values):
+// the on-site entry and 8 real hop entries, 4 imaginary ones.  Chunks of this
+// shape take a fully unrolled row sum (compile-time slot indices, every
+// shared-memory load of the row issued before its multiply-adds).
+constexpr int FP_FULL_RE = 9, FP_FULL_IM = 4;
+
+// fn(K0), fn(K0 + 1), ..., fn(K1 - 1) with compile-time indices.
+template <int K0, int K1, typename Fn>
+__device__ __forceinline__ void unrolled(Fn &&fn) {
+    if constexpr (K0 < K1) {
+        fn(K0);
+        unrolled<K0 + 1, K1>(fn);
+    }
+}
 
 }  // namespace
 
@@ -452,8 +466,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                         acc[q].x = -wo[q].x;
                         acc[q].y = -wo[q].y;
                     }
-#pragma unroll 4
-                    for (int kk = 0; kk < nre; ++kk) {
+                    auto madd_re = [&](int kk) {
                         E v[VPT];
                         vrow(kk, v);
                         const float h = val_s[kk * FP_C + rr];
@@ -462,9 +475,8 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                             acc[q].x = fmaf(h, v[q].x, acc[q].x);
                             acc[q].y = fmaf(h, v[q].y, acc[q].y);
                         }
-                    }
-#pragma unroll 4
-                    for (int kk = nre; kk < len; ++kk) {
+                    };
+                    auto madd_im = [&](int kk) {
                         E v[VPT];
                         vrow(kk, v);
                         const float h = val_s[kk * FP_C + rr];
@@ -473,6 +485,15 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                             acc[q].x = fmaf(-h, v[q].y, acc[q].x);
                             acc[q].y = fmaf(h, v[q].x, acc[q].y);
                         }
+                    };
+                    if (nre == FP_FULL_RE && len == FP_FULL_RE + FP_FULL_IM) {
+                        unrolled<0, FP_FULL_RE>(madd_re);
+                        unrolled<FP_FULL_RE, FP_FULL_RE + FP_FULL_IM>(madd_im);
+                    } else {
+#pragma unroll 4
+                        for (int kk = 0; kk < nre; ++kk) madd_re(kk);
+#pragma unroll 4
+                        for (int kk = nre; kk < len; ++kk) madd_im(kk);
                     }
                     E xn[VPT];
 #pragma unroll
@@ -500,8 +521,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                         s2[q] = make_float2(-wo[q].x, -wo[q].y);
                         e2[q] = make_float2(-wo[q].z, -wo[q].w);
                     }
-#pragma unroll 2
-                    for (int kk = 0; kk < nre; ++kk) {
+                    auto madd_re = [&](int kk) {
                         E v[VPT];
                         vrow(kk, v);
                         const float2 h = val_s[kk * FP_C + rr];
@@ -512,14 +532,8 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                         for (int q = 0; q < VPT; ++q)
                             dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y),
                                     make_float2(v[q].z, v[q].w));
-                    }
-#pragma unroll
-                    for (int q = 0; q < VPT; ++q) {
-                        s2[q] = swap2(s2[q]);
-                        e2[q] = swap2(e2[q]);
-                    }
-#pragma unroll 2
-                    for (int kk = nre; kk < len; ++kk) {
+                    };
+                    auto madd_im = [&](int kk) {
                         E v[VPT];
                         vrow(kk, v);
                         const float2 h = val_s[kk * FP_C + rr];
@@ -530,11 +544,26 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                         for (int q = 0; q < VPT; ++q)
                             dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y),
                                     make_float2(v[q].z, v[q].w));
-                    }
+                    };
+                    auto swap_acc = [&]() {
 #pragma unroll
-                    for (int q = 0; q < VPT; ++q) {
-                        s2[q] = swap2(s2[q]);
-                        e2[q] = swap2(e2[q]);
+                        for (int q = 0; q < VPT; ++q) {
+                            s2[q] = swap2(s2[q]);
+                            e2[q] = swap2(e2[q]);
+                        }
+                    };
+                    if (nre == FP_FULL_RE && len == FP_FULL_RE + FP_FULL_IM) {
+                        unrolled<0, FP_FULL_RE>(madd_re);
+                        swap_acc();
+                        unrolled<FP_FULL_RE, FP_FULL_RE + FP_FULL_IM>(madd_im);
+                        swap_acc();
+                    } else {
+#pragma unroll 2
+                        for (int kk = 0; kk < nre; ++kk) madd_re(kk);
+                        swap_acc();
+#pragma unroll 2
+                        for (int kk = nre; kk < len; ++kk) madd_im(kk);
+                        swap_acc();
                     }
                     if (MOM) {
                         if constexpr (SM) lds_row(rows_s + (own_off + rr) * NB, u);
