@@ -468,7 +468,8 @@ cfd_status cfd_workspace_status(const void *work, cudaStream_t stream);
  * The scratch is a 64 MiB array inside the library, one copy on every device
  * that loads it, kept until the process exits.  Problems whose
  * cfd_filter_workspace(...) exceeds CFD_NOALLOC_SCRATCH_BYTES are rejected
- * with CFD_ERR_ARG (for complex double roughly N (32 n_b + 208) bytes <= 64 MiB, e.g. N <= 54000 at n_b = 32).
+ * with CFD_ERR_ARG (for complex double roughly N (32 n_b + 208) bytes, plus 34 per row at n_b = 32,
+ * <= 64 MiB, e.g. N <= 51000 at n_b = 32).
  * Nothing is allocated: no cudaMalloc/cudaFree and no allocating library call.
  *
  * Argument errors are reported as by cfd_filter before the size check.
