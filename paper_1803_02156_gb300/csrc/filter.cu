@@ -327,11 +327,10 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
     // footprint-staged general steps (complex float, or double-word), with
     // the chunks' footprints found once per call
     FpView F;
-    if (P.footprint >= 0 && !P.persistent && P.staged >= 1 && !P.chunk_rid && ws.fp &&
-        (dw || std::is_same<T, float>::value)) {
+    if (P.footprint >= 0 && !P.persistent && P.staged >= 1 && ws.fp && (dw || std::is_same<T, float>::value)) {
         int fmax = footprint_rows_cap(H, n_b, vpt, dw);
         if (P.footprint > 0) fmax = std::min(fmax, P.footprint);
-        if (fmax > 0) CFD_TRY(launch_footprint(H, fmax, ws.fp, ws.fp_bytes, &F, stream));
+        if (fmax > 0) CFD_TRY(launch_footprint(H, P.chunk_rid, fmax, ws.fp, ws.fp_bytes, &F, stream));
     }
     C *va = static_cast<C *>(ws.va), *vb = static_cast<C *>(ws.vb);
     const int n_blocks = X.n_cols / n_b;

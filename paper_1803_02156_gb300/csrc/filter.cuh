@@ -134,12 +134,12 @@ struct FpView {
 size_t footprint_bytes(int64_t N);
 // Footprint rows one stage of the footprint step holds for H at n_b / vpt
 // (complex float, or complex double in double-word arithmetic); 0 when the
-// step does not apply (it needs packed values, C = 32, sigma = 1, n_b = 32,
-// two vectors per thread).
+// step does not apply (it needs packed values, C = 32, sigma = 1, n_b = 32).
 int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw);
-// Builds the footprints of H's chunks (at most fmax rows each) in buf.
-cfd_status launch_footprint(const cfd_matrix *H, int fmax, void *buf, size_t buf_bytes, FpView *out,
-                            cudaStream_t stream);
+// Builds the footprints of H's chunks (at most fmax rows each) in buf; in a
+// batch (chunk_rid set) each descriptor also names its chunk's realisation.
+cfd_status launch_footprint(const cfd_matrix *H, const int32_t *chunk_rid, int fmax, void *buf, size_t buf_bytes,
+                            FpView *out, cudaStream_t stream);
 // One general step with the footprints staged (complex float; complex double
 // in double-word arithmetic, last: X written back as complex double).
 cfd_status launch_step_fp(const StepArgs<float> &A, const FpView &F, int nb, int vpt, int grid_cap, cudaStream_t s);

@@ -84,10 +84,11 @@ __host__ __device__ inline FpLayout fp_layout(int slots_cap, int val_bytes, int 
 // descriptor desc[c 32 + l] (32 int2, one coalesced 256-byte load for a
 // warp) holds in word 0 {chunk_len, ranges (-1: not staged)}, word 1
 // {footprint rows, row of the chunk's first own row}, word 2 the chunk's
-// first slot (low, high 32 bits), words 8 + r {first row, rows} of range r.
+// first slot (low, high 32 bits), word 3 {the chunk's realisation in a batch,
+// 0}, words 8 + r {first row, rows} of range r.
 __global__ void __launch_bounds__(256) k_footprint(const int32_t *col, const int64_t *chunk_ptr,
                                                    const int32_t *chunk_len, int64_t n_rows, int64_t n_chunks,
-                                                   int fmax, uint16_t *lcol, int2 *desc) {
+                                                   const int32_t *chunk_rid, int fmax, uint16_t *lcol, int2 *desc) {
     __shared__ int key[FP_KEYS];
     __shared__ int rs[FP_RMAX], re[FP_RMAX], ro[FP_RMAX];
     __shared__ int s_nr, s_total;
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(256) k_footprint(const int32_t *col, const int
             if (tid == 0) d = make_int2(cl, nr);
             else if (tid == 1) d = make_int2(s_total, nr >= 0 ? local((int)r0) : 0);
             else if (tid == 2) d = make_int2((int)(uint32_t)base, (int)(uint32_t)((uint64_t)base >> 32));
+            else if (tid == 3) d = make_int2(chunk_rid ? chunk_rid[c] : 0, 0);
             else if (tid >= 8 && tid - 8 < nr) d = make_int2(rs[tid - 8], re[tid - 8] - rs[tid - 8]);
             desc[c * 32 + tid] = d;
         }
@@ -268,23 +270,27 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
     using E = typename FpTypes<MODE>::E;
     using V = typename FpTypes<MODE>::V;
     constexpr bool DW = MODE == FPM_DW;
-    constexpr bool STRIDED = DW;
+    // a thread's vectors in units of G consecutive ones (16 bytes): unit u of
+    // the row's NB vectors starts at u TPR G + (lane % TPR) G, so the 16-byte
+    // shared-memory loads of the threads of a row are contiguous
+    constexpr int G = 16 / (int)sizeof(E);
+    static_assert(VPT % G == 0, "vectors per thread in whole 16-byte units");
     constexpr int TPR = NB / VPT;
     constexpr int RPW = 32 / TPR;
     constexpr int ROWS_PASS = W * RPW;
     constexpr int RB = NB * (int)sizeof(E);
     static_assert(TPR >= 1 && TPR <= 32 && (32 % TPR) == 0, "bad thread split");
-    static_assert(!(STRIDED && XST), "staged X rows are read with the consecutive layout");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[S];
     __shared__ __align__(8) uint64_t empty[S];
     __shared__ int4 s_info[S];
+    __shared__ float4 s_w[S];     // the chunk's weight g_p c_p: {as a float, double-word hi, lo, 0}
     __shared__ int s_abort;
     const FpLayout L = fp_layout(slots_cap, (int)sizeof(V), RB, F.fmax, XST);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = lane / TPR;
     const int jt = lane % TPR;
-    auto jq = [&](int q) { return STRIDED ? jt + q * TPR : jt * VPT + q; };
+    auto jq = [&](int q) { return (q / G) * TPR * G + jt * G + q % G; };
     const int64_t n_rows = A.H.n_rows;
     const int64_t n_chunks = (n_rows + FP_C - 1) / FP_C;
     const E *vin = reinterpret_cast<const E *>(A.vin);
@@ -296,11 +302,6 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
     const long long limit = A.staged == 2 ? (1LL << 24) : (1LL << 32);
     volatile int *abort_flag = &s_abort;
 
-    // the step's weight g_p c_p: as a float, or as a double-word (gh, gl)
-    const double gd = A.gc[A.p];
-    const float g0 = (float)gd;
-    const float gh = __double2float_rn(gd);
-    const float gl = __double2float_rn(gd - (double)gh);
     MomentAcc<float> uu[VPT], wu[VPT];                       // complex float
     float2 uu_s2[VPT], uu_e2[VPT], wu_s2[VPT], wu_e2[VPT];   // double-word, per lane (re, im)
 #pragma unroll
@@ -333,6 +334,12 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
 
     if (warp == W) {
         // ------------------------------------------------------ producer --
+        // a weight as a float and as a double-word {hi, lo}
+        auto weight = [](double gd) {
+            const float gh = __double2float_rn(gd);
+            return make_float4(gh, gh, __double2float_rn(gd - (double)gh), 0.f);
+        };
+        const float4 w_step = A.chunk_rid ? make_float4(0.f, 0.f, 0.f, 0.f) : weight(A.gc[A.p]);
         // chunk c into stage s from its descriptor (lane l holds word l)
         auto issue = [&](int64_t c, int s, int2 d) {
             unsigned char *st = smem_raw + (size_t)s * L.stage;
@@ -358,7 +365,12 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
             off -= g.y;
             const uint32_t bytes = nslot * (uint32_t)sizeof(V) + (uint32_t)own * RB * (XST ? 2u : 1u) +
                                    (nr >= 0 ? nslot * 2u + (uint32_t)tot * RB : 0u) + tx_extra;
-            if (lane == 0) s_info[s] = make_int4(cl, nr, own_off, own);
+            const int rid = __shfl_sync(0xffffffffu, d.x, 3);
+            if (lane == 0) {
+                s_info[s] = make_int4(cl, nr, own_off, own);
+                // the step's weight g_p c_p (in a batch, that of the chunk's realisation)
+                s_w[s] = A.chunk_rid ? weight(__ldg(A.rcoef + (int64_t)rid * A.rcoef_ld + 2 + A.p)) : w_step;
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (lane == 0) mbar_expect_tx(&full[s], bytes);
             __syncwarp();
@@ -393,27 +405,30 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
     } else {
         // ----------------------------------------------------- consumers --
         auto lds_row = [&](const E *rowp, E (&v)[VPT]) {     // shared memory, or plain global loads
-            if constexpr (STRIDED) {
 #pragma unroll
-                for (int q = 0; q < VPT; ++q) v[q] = rowp[jq(q)];
-            } else {
-                ld_elems<E, VPT>(rowp + jt * VPT, v);
+            for (int u = 0; u < VPT / G; ++u) {
+                E w[G];
+                ld_elems<E, G>(rowp + u * TPR * G + jt * G, w);
+#pragma unroll
+                for (int t = 0; t < G; ++t) v[u * G + t] = w[t];
             }
         };
         auto ldg_row = [&](const E *rowp, E (&v)[VPT]) {     // read-only global loads
-            if constexpr (STRIDED) {
 #pragma unroll
-                for (int q = 0; q < VPT; ++q) v[q] = __ldg(rowp + jq(q));
-            } else {
-                ldg_elems<E, VPT>(rowp + jt * VPT, v);
+            for (int u = 0; u < VPT / G; ++u) {
+                E w[G];
+                ldg_elems<E, G>(rowp + u * TPR * G + jt * G, w);
+#pragma unroll
+                for (int t = 0; t < G; ++t) v[u * G + t] = w[t];
             }
         };
         auto st_row = [&](E *rowp, const E (&v)[VPT]) {
-            if constexpr (STRIDED) {
 #pragma unroll
-                for (int q = 0; q < VPT; ++q) rowp[jq(q)] = v[q];
-            } else {
-                st_elems<E, VPT>(rowp + jt * VPT, v);
+            for (int u = 0; u < VPT / G; ++u) {
+                E w[G];
+#pragma unroll
+                for (int t = 0; t < G; ++t) w[t] = v[u * G + t];
+                st_elems<E, G>(rowp + u * TPR * G + jt * G, w);
             }
         };
         // this warp's rows of one chunk from stage s; SM: V_cur rows from the
@@ -428,6 +443,8 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
             constexpr bool SM = decltype(sm_tag)::value;
             const int4 inf = s_info[s];
             const int cl = inf.x, own_off = inf.z, own = inf.w;
+            const float4 wv = s_w[s];
+            const float g0 = wv.x, gh = wv.y, gl = wv.z;
             const int nre = cl & 0xffff, len = nre + (cl >> 16);
             const unsigned char *st = smem_raw + (size_t)s * L.stage;
             const uint16_t *lc_s = reinterpret_cast<const uint16_t *>(st + L.lcol);
@@ -637,7 +654,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                 lanes(wu_s2[q], wu_e2[q], wu[q]);
             }
         }
-        reduce_moments<float, NB, VPT, W + 1, STRIDED>(A.partial, A.ticket, A.dots, uu, wu);
+        reduce_moments<float, NB, VPT, W + 1, G>(A.partial, A.ticket, A.dots, uu, wu);
     }
 }
 
@@ -654,28 +671,37 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
 #ifndef CFD_FP_DW_STAGES
 #define CFD_FP_DW_STAGES 2
 #endif
-// Consumer warps of the CTA (one CTA per SM, plus the producer warp).
+// Vectors per thread, and consumer warps of the CTA (one CTA per SM, plus
+// the producer warp; 0: one row per thread and chunk, n_b / vpt warps).
+#ifndef CFD_FP_C64_VPT
+#define CFD_FP_C64_VPT 2
+#endif
+#ifndef CFD_FP_DW_VPT
+#define CFD_FP_DW_VPT 2
+#endif
 #ifndef CFD_FP_C64_WARPS
-#define CFD_FP_C64_WARPS 16
+#define CFD_FP_C64_WARPS 0
 #endif
 #ifndef CFD_FP_DW_WARPS
-#define CFD_FP_DW_WARPS 16
+#define CFD_FP_DW_WARPS 0
 #endif
 
 namespace {
 
-constexpr int FP_NB = 32, FP_VPT = 2;
+constexpr int FP_NB = 32;
 
 template <int MODE> struct FpConf;
 template <> struct FpConf<FPM_C64> {
     static constexpr int S = CFD_FP_C64_STAGES;
     static constexpr bool XST = CFD_FP_C64_XST != 0;
-    static constexpr int W = CFD_FP_C64_WARPS;
+    static constexpr int VPT = CFD_FP_C64_VPT;
+    static constexpr int W = CFD_FP_C64_WARPS ? CFD_FP_C64_WARPS : FP_NB / VPT;
 };
 template <> struct FpConf<FPM_DW> {
     static constexpr int S = CFD_FP_DW_STAGES;
     static constexpr bool XST = false;
-    static constexpr int W = CFD_FP_DW_WARPS;
+    static constexpr int VPT = CFD_FP_DW_VPT;
+    static constexpr int W = CFD_FP_DW_WARPS ? CFD_FP_DW_WARPS : FP_NB / VPT;
 };
 
 // Dynamic shared memory a CTA may take next to the kernel's static shared
@@ -697,9 +723,9 @@ cfd_status fp_smem_budget(size_t *out) {
         // the moments variant carries the reduction's static arrays
         cudaFuncAttributes fa{};
         constexpr int W = FpConf<MODE>::W;
-        CFD_CUDA(cudaFuncGetAttributes(&fa, k_cheb_step_fp<MODE, FP_NB, FP_VPT, true, false, S, XST, W>));
+        CFD_CUDA(cudaFuncGetAttributes(&fa, k_cheb_step_fp<MODE, FP_NB, FpConf<MODE>::VPT, true, false, S, XST, W>));
         cudaFuncAttributes fb{};
-        CFD_CUDA(cudaFuncGetAttributes(&fb, k_cheb_step_fp<MODE, FP_NB, FP_VPT, true, true, S, XST, W>));
+        CFD_CUDA(cudaFuncGetAttributes(&fb, k_cheb_step_fp<MODE, FP_NB, FpConf<MODE>::VPT, true, true, S, XST, W>));
         const size_t stat = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
         cache[dev] = (size_t)optin > stat + 1024 ? (size_t)optin - stat - 1024 : 1;
     }
@@ -738,7 +764,7 @@ cfd_status launch_fp_t(const StepArgs<typename FpTypes<MODE>::T> &A, const FpVie
     CFD_TRY(fp_smem_budget<MODE>(&budget));
     if (smem > budget) return fail(CFD_ERR_ARG, "footprint stages of %d rows need %zu bytes of shared memory", F.fmax, smem);
     constexpr int W = FpConf<MODE>::W;
-    auto kern = k_cheb_step_fp<MODE, FP_NB, FP_VPT, MOM, LAST, S, XST, W>;
+    auto kern = k_cheb_step_fp<MODE, FP_NB, FpConf<MODE>::VPT, MOM, LAST, S, XST, W>;
     struct Cache {
         std::mutex mu;
         int occ[64];
@@ -776,10 +802,10 @@ cfd_status launch_fp_t(const StepArgs<typename FpTypes<MODE>::T> &A, const FpVie
 
 template <typename T>
 cfd_status fp_check(const StepArgs<T> &A, const FpView &F, int nb, int vpt) {
-    if (nb != FP_NB || vpt != FP_VPT)
-        return fail(CFD_ERR_INTERNAL, "footprint step built for n_b = %d, %d vectors per thread", FP_NB, FP_VPT);
-    if (!A.H.packed || A.H.log2C != 5 || A.H.perm || A.chunk_rid)
-        return fail(CFD_ERR_INTERNAL, "footprint step needs a packed C = 32, sigma = 1 matrix, one realisation");
+    (void)vpt;    // the footprint step's own thread split; results do not depend on it
+    if (nb != FP_NB) return fail(CFD_ERR_INTERNAL, "footprint step built for n_b = %d", FP_NB);
+    if (!A.H.packed || A.H.log2C != 5 || A.H.perm || (A.chunk_rid && !A.rcoef))
+        return fail(CFD_ERR_INTERNAL, "footprint step needs a packed C = 32, sigma = 1 matrix");
     if (A.ldin != FP_NB || A.ldw != FP_NB || !A.x || !A.status || !A.prep_val || F.fmax <= 0 || !F.lcol)
         return fail(CFD_ERR_INTERNAL, "footprint step arguments incomplete");
     return CFD_OK;
@@ -794,7 +820,8 @@ size_t footprint_bytes(int64_t N) {
 
 int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw) {
     const int slots_bound = (H->flags >> CFD_MATRIX_SLOTS_SHIFT) & 0xff;
-    if (nb != FP_NB || vpt != FP_VPT || H->C != FP_C || H->perm || !(H->flags & CFD_MATRIX_PACKED)) return 0;
+    (void)vpt;
+    if (nb != FP_NB || H->C != FP_C || H->perm || !(H->flags & CFD_MATRIX_PACKED)) return 0;
     if (slots_bound < 1 || slots_bound * FP_C + FP_C > FP_KEYS) return 0;
     if (H->n_rows >= (int64_t)INT_MAX) return 0;
     if (dw ? H->prec != CFD_C128 : H->prec != CFD_C64) return 0;
@@ -802,8 +829,8 @@ int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw) {
     return std::min(cap, 65535);
 }
 
-cfd_status launch_footprint(const cfd_matrix *H, int fmax, void *buf, size_t buf_bytes, FpView *out,
-                            cudaStream_t stream) {
+cfd_status launch_footprint(const cfd_matrix *H, const int32_t *chunk_rid, int fmax, void *buf, size_t buf_bytes,
+                            FpView *out, cudaStream_t stream) {
     const int64_t n_chunks = (H->n_rows + FP_C - 1) / FP_C;
     if (H->C != FP_C || H->n_chunks != n_chunks) return fail(CFD_ERR_INTERNAL, "footprint needs C = 32");
     if (H->n_slots > (int64_t)kMaxRowSlots * (H->n_rows + 127) || footprint_bytes(H->n_rows) > buf_bytes)
@@ -812,7 +839,8 @@ cfd_status launch_footprint(const cfd_matrix *H, int fmax, void *buf, size_t buf
     uint16_t *lcol = c.take<uint16_t>((size_t)kMaxRowSlots * (size_t)(H->n_rows + 127));
     int2 *desc = c.take<int2>((size_t)n_chunks * 32);
     const int grid = (int)std::min<int64_t>(n_chunks, (int64_t)sm_count() * 8);
-    k_footprint<<<grid, 256, 0, stream>>>(H->col, H->chunk_ptr, H->chunk_len, H->n_rows, n_chunks, fmax, lcol, desc);
+    k_footprint<<<grid, 256, 0, stream>>>(H->col, H->chunk_ptr, H->chunk_len, H->n_rows, n_chunks, chunk_rid, fmax,
+                                          lcol, desc);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     out->lcol = lcol;

@@ -522,9 +522,10 @@ template <> struct MomentRed<float> {
 // Deterministic reduction of the threads' moment sums: warps (shuffles), the
 // CTA (shared memory, fixed order), then across CTAs by the last CTA to finish
 // (ticket counter), each in a fixed order.  WARPS: the CTA's warps.  A
-// thread's vectors are (lane % TPR) VPT + q, or with STRIDED (lane % TPR) +
-// q TPR, q < VPT.
-template <typename T, int NB, int VPT, int WARPS = STEP_WARPS, bool STRIDED = false>
+// thread's vectors q < VPT come in units of G consecutive vectors: vector q
+// is (q / G) TPR G + (lane % TPR) G + q % G (G = VPT: VPT consecutive
+// vectors; G = 1: vectors lane % TPR + q TPR).
+template <typename T, int NB, int VPT, int WARPS = STEP_WARPS, int G = VPT>
 __device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket, double *dots,
                                                MomentAcc<T> (&uu)[VPT], MomentAcc<T> (&wu)[VPT]) {
     using Op = MomentRed<T>;
@@ -534,7 +535,7 @@ __device__ __forceinline__ void reduce_moments(double *partial, unsigned *ticket
     const int warp = threadIdx.x >> 5;
     const int sub = lane / TPR;
     const int jt = lane % TPR;
-    auto jq = [&](int q) { return STRIDED ? jt + q * TPR : jt * VPT + q; };
+    auto jq = [&](int q) { return (q / G) * TPR * G + jt * G + q % G; };
     __shared__ R red[WARPS][NB][2];
     __shared__ bool last_cta;
     R s_uu[VPT], s_wu[VPT];
