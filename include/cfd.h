@@ -292,13 +292,14 @@ typedef struct cfd_filter_opts {
                              are kept).  Results are bit for bit those of graph 0.  The first call of each
                              argument set captures, so make it outside any capture of your own. */
     int32_t footprint;    /* general steps of complex-float filters and double-word complex-double filters
-                             (packed values, C = 32, sigma = 1, n_b = 32, two vectors per thread, one
-                             realisation): 0 (default) stages each chunk's footprint, the rows of V_cur its
-                             slots read, by TMA bulk copies into shared memory before the chunk is computed
-                             (the row ranges are found once per call); -1 never (every slot's V_cur row is
-                             gathered from global memory); n > 0 as 0 with at most n footprint rows per
-                             chunk (chunks with more are gathered from global memory).  Results do not depend
-                             on it (filtered block bit for bit; moments to the order of their sums). */
+                             (packed values, C = 32, sigma = 1, n_b = 32): 0 (default) stages each chunk's
+                             footprint, the rows of V_cur its slots read, by TMA bulk copies into shared
+                             memory before the chunk is computed (the row ranges are found once per call),
+                             for matrices of at least 16 chunks per SM (smaller ones keep the gathered
+                             steps); -1 never (every slot's V_cur row is gathered from global memory); n > 0
+                             the footprint steps at any size, with at most n footprint rows per chunk
+                             (chunks with more are gathered from global memory).  Results do not depend on
+                             it (filtered block bit for bit; moments to the order of their sums). */
 } cfd_filter_opts;
 
 /* cfd_filter with explicit kernel options (the autotuner's knobs besides n_b,
@@ -624,6 +625,20 @@ size_t cfd_gram_workspace(int64_t N, int n_x, int n_y);
 cfd_status cfd_block_gram(cfd_block X, cfd_block Y, void *S, int64_t lds, void *work, size_t work_bytes,
                           cudaStream_t stream);
 
+/*
+ * cfd_block_gram with a choice of arithmetic: arith 0 as cfd_block_gram (fp64
+ * on the FP64 tensor cores), 1 double-word arithmetic on the fp32 pipe: every
+ * double split once into hi + lo floats, every multiply-add a double-word one
+ * (Dekker's product, Knuth's sum, the errors collected in a second float),
+ * each split's sums accurate to a few units of 2^-48 of their terms (2^-53
+ * natively), the splits folded in fp64 in the same fixed order.  GB300 runs
+ * fp64 at 1/64 of the fp32 rate, so the double-word Gram is several times
+ * faster.  Same workspace (cfd_gram_workspace); CFD_ERR_ARG for another
+ * arith.  Asynchronous.
+ */
+cfd_status cfd_block_gram_ex(cfd_block X, cfd_block Y, void *S, int64_t lds, void *work, size_t work_bytes,
+                             int arith, cudaStream_t stream);
+
 /* Device scratch bytes of cfd_eigh for order n. */
 size_t cfd_eigh_workspace(int n);
 
@@ -656,6 +671,12 @@ size_t cfd_orthogonalize_workspace(int64_t N, int n_s);
 cfd_status cfd_orthogonalize(cfd_block X, double tol, int *rank, void *work, size_t work_bytes,
                              cudaStream_t stream);
 
+/* cfd_orthogonalize with a choice of arithmetic for its Gram matrices and
+ * projections: arith 0 fp64 (as cfd_orthogonalize), 1 double-word arithmetic
+ * on the fp32 pipe (as cfd_block_gram_ex).  Same workspace. */
+cfd_status cfd_orthogonalize_ex(cfd_block X, double tol, int *rank, void *work, size_t work_bytes, int arith,
+                                cudaStream_t stream);
+
 /* Device scratch bytes of cfd_rayleigh_ritz for an N x n_s block. */
 size_t cfd_rayleigh_ritz_workspace(int64_t N, int n_s);
 
@@ -675,9 +696,10 @@ cfd_status cfd_rayleigh_ritz(const cfd_matrix *H, cfd_block X, double *evals, do
 typedef enum cfd_policy {
     CFD_POLICY_FP64 = 0,     /* every filter application in fp64 */
     CFD_POLICY_MIXED = 1,    /* fp32 filter until it stalls, then fp64; SVQB and RR always fp64 */
-    CFD_POLICY_FP64_DW = 2,  /* as FP64 with the filter's general steps in double-word arithmetic on the
-                                fp32 pipe (cfd_filter_opts.arith = 1; H needs packed values) */
-    CFD_POLICY_MIXED_DW = 3  /* as MIXED with the fp64 filter phase in double-word arithmetic */
+    CFD_POLICY_FP64_DW = 2,  /* as FP64 with double-word arithmetic on the fp32 pipe for the filter's
+                                general steps (cfd_filter_opts.arith = 1; H needs packed values) and for the
+                                Gram matrices and projections of SVQB and RR (cfd_block_gram_ex arith 1) */
+    CFD_POLICY_MIXED_DW = 3  /* as MIXED with the fp64 filter phase, SVQB and RR in double-word arithmetic */
 } cfd_policy;
 
 typedef struct cfd_solve_params {

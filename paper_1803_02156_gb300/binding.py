@@ -169,12 +169,16 @@ _PROTOS = {
     "cfd_gram_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
     "cfd_block_gram": (ctypes.c_int, [cfd_block, cfd_block, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                       ctypes.c_size_t, ctypes.c_void_p]),
+    "cfd_block_gram_ex": (ctypes.c_int, [cfd_block, cfd_block, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     "cfd_eigh_workspace": (ctypes.c_size_t, [ctypes.c_int]),
     "cfd_eigh": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "cfd_orthogonalize_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int]),
     "cfd_orthogonalize": (ctypes.c_int, [cfd_block, ctypes.c_double, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
                                          ctypes.c_size_t, ctypes.c_void_p]),
+    "cfd_orthogonalize_ex": (ctypes.c_int, [cfd_block, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     "cfd_rayleigh_ritz_workspace": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int]),
     "cfd_rayleigh_ritz": (ctypes.c_int, [ctypes.POINTER(cfd_matrix), cfd_block, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -564,13 +568,17 @@ def cfd_spectral_bounds(H, steps=40, seed=3, stream=None):
     return lo.value, hi.value
 
 
-def cfd_block_gram(X, Y, stream=None):
-    """S = X^H Y (complex double device tensor)."""
+def cfd_block_gram(X, Y, stream=None, arith=0):
+    """S = X^H Y (complex double device tensor); arith 1: double-word
+    arithmetic on the fp32 pipe (cfd_block_gram_ex)."""
     bx, by = block_of(X), block_of(Y)
     S = torch.empty(bx.n_cols, by.n_cols, dtype=torch.complex128, device=X.device)
     ws = lib().cfd_gram_workspace(bx.n_rows, bx.n_cols, by.n_cols)
     work = _workspace(ws, X.device)
-    _check(lib().cfd_block_gram(bx, by, _ptr(S), S.stride(0), _ptr(work), ws, _stream(stream)))
+    if arith:
+        _check(lib().cfd_block_gram_ex(bx, by, _ptr(S), S.stride(0), _ptr(work), ws, arith, _stream(stream)))
+    else:
+        _check(lib().cfd_block_gram(bx, by, _ptr(S), S.stride(0), _ptr(work), ws, _stream(stream)))
     return S
 
 
@@ -586,13 +594,17 @@ def cfd_eigh(A, stream=None):
     return ev, Q
 
 
-def cfd_orthogonalize(X, tol=0.0, stream=None):
-    """SVQB-orthonormalise the columns of X in place; returns the rank of the first pass."""
+def cfd_orthogonalize(X, tol=0.0, stream=None, arith=0):
+    """SVQB-orthonormalise the columns of X in place; returns the rank of the
+    first pass.  arith 1: Grams and projections in double-word arithmetic."""
     blk = block_of(X)
     ws = lib().cfd_orthogonalize_workspace(blk.n_rows, blk.n_cols)
     work = _workspace(ws, X.device)
     rank = ctypes.c_int()
-    _check(lib().cfd_orthogonalize(blk, tol, ctypes.byref(rank), _ptr(work), ws, _stream(stream)))
+    if arith:
+        _check(lib().cfd_orthogonalize_ex(blk, tol, ctypes.byref(rank), _ptr(work), ws, arith, _stream(stream)))
+    else:
+        _check(lib().cfd_orthogonalize(blk, tol, ctypes.byref(rank), _ptr(work), ws, _stream(stream)))
     return rank.value
 
 

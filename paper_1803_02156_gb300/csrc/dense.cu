@@ -159,7 +159,14 @@ int gram_splits(int64_t K, int ma, int nb) {
 
 size_t gram_workspace(int64_t K, int na, int nbc) {
     int ma = 2 * na, nb = 2 * nbc;
-    return round_up((size_t)gram_splits(K, ma, nb) * ma * nb * sizeof(double), 256);
+    const int splits = std::max(gram_splits(K, ma, nb), gram_dw_split_cap(K, ma, nb));
+    return round_up((size_t)splits * ma * nb * sizeof(double), 256);
+}
+
+void launch_gram_fold(const double *part, int splits, int ma, int nb, double2 *S, int64_t lds, bool herm,
+                      cudaStream_t stream) {
+    const int n = (ma / 2) * (nb / 2);
+    k_gram_fold<<<(n + 255) / 256, 256, 0, stream>>>(part, std::max(splits, 1), ma, nb, S, lds, 0, herm ? 1 : 0);
 }
 
 cfd_status gram(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nbc, int64_t K,

@@ -21,10 +21,24 @@ size_t gram_workspace(int64_t K, int na, int nb);
 cfd_status gram(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nb, int64_t K,
                 double2 *S, int64_t lds, double *work, cudaStream_t stream, bool herm = false);
 
+// The same Gram in double-word arithmetic on the fp32 pipe (dense_dw.cu):
+// same arguments and workspace; each split's sums accurate to a few units of
+// 2^-48 of their terms instead of 2^-53.  gram_dw_split_cap: the most K-splits
+// it uses (gram_workspace holds that many partials); launch_gram_fold: the
+// fixed-order fold of the partials into S (shared with gram).
+cfd_status gram_dw(const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nb, int64_t K,
+                   double2 *S, int64_t lds, double *work, cudaStream_t stream, bool herm = false);
+int gram_dw_split_cap(int64_t K, int ma, int nb);
+void launch_gram_fold(const double *part, int splits, int ma, int nb, double2 *S, int64_t lds, bool herm,
+                      cudaStream_t stream);
+
 // X[:, 0:n_out] <- X[:, 0:n_in] M (M n_in x n_out complex, ld ldm), in place, n_out <= n_in.
 size_t project_workspace(int n_in, int n_out);
 cfd_status project_inplace(double2 *X, int64_t ldx, int64_t n_rows, int n_in, const double2 *M, int64_t ldm,
                            int n_out, double *work, cudaStream_t stream);
+// The same projection in double-word arithmetic (dense_dw.cu), same workspace.
+cfd_status project_inplace_dw(double2 *X, int64_t ldx, int64_t n_rows, int n_in, const double2 *M, int64_t ldm,
+                              int n_out, double *work, cudaStream_t stream);
 
 // Eigen-decomposition of the Hermitian part of A (n x n): eigenvalues ascending
 // in evals[n], eigenvectors in the columns of Q (ld ldq).  sweeps (host, nullable)

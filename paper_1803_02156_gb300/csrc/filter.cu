@@ -328,7 +328,7 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
     // the chunks' footprints found once per call
     FpView F;
     if (P.footprint >= 0 && !P.persistent && P.staged >= 1 && ws.fp && (dw || std::is_same<T, float>::value)) {
-        int fmax = footprint_rows_cap(H, n_b, vpt, dw);
+        int fmax = footprint_rows_cap(H, n_b, vpt, dw, P.footprint > 0);
         if (P.footprint > 0) fmax = std::min(fmax, P.footprint);
         if (fmax > 0) CFD_TRY(launch_footprint(H, P.chunk_rid, fmax, ws.fp, ws.fp_bytes, &F, stream));
     }

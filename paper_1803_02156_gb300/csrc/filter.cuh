@@ -134,8 +134,9 @@ struct FpView {
 size_t footprint_bytes(int64_t N);
 // Footprint rows one stage of the footprint step holds for H at n_b / vpt
 // (complex float, or complex double in double-word arithmetic); 0 when the
-// step does not apply (it needs packed values, C = 32, sigma = 1, n_b = 32).
-int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw);
+// step does not apply (it needs packed values, C = 32, sigma = 1, n_b = 32)
+// or, unless any_size, when H has too few chunks for it to pay.
+int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw, bool any_size);
 // Builds the footprints of H's chunks (at most fmax rows each) in buf; in a
 // batch (chunk_rid set) each descriptor also names its chunk's realisation.
 cfd_status launch_footprint(const cfd_matrix *H, const int32_t *chunk_rid, int fmax, void *buf, size_t buf_bytes,
@@ -163,7 +164,8 @@ struct FilterPlan {
     int gather = 0;
     int fixed_chunk = 0;
     int arith = ARITH_NATIVE;
-    int footprint = 0;                    // footprint steps: 0 where they apply, < 0 never, > 0 at most this many rows
+    int footprint = 0;                    // footprint steps: 0 where they apply and pay, < 0 never,
+                                          // > 0 wherever they apply, at most this many rows a chunk
     double alpha = 0, beta = 0;
     const int32_t *chunk_rid = nullptr;   // batch: chunk -> realisation
     const double *rcoef = nullptr;        // batch: per realisation {alpha, beta, weights}

@@ -53,11 +53,25 @@ size_t svqb_workspace(int64_t N, int n) {
     return round_up(c.off, 256);
 }
 
+// The N-row Gram and projection in native fp64 (FP64 tensor cores) or in
+// double-word arithmetic on the fp32 pipe (dw).
+static cfd_status gram_n(bool dw, const double2 *X, int64_t ldx, int na, const double2 *Y, int64_t ldy, int nb,
+                         int64_t K, double2 *S, int64_t lds, double *work, cudaStream_t stream, bool herm) {
+    return dw ? gram_dw(X, ldx, na, Y, ldy, nb, K, S, lds, work, stream, herm)
+              : gram(X, ldx, na, Y, ldy, nb, K, S, lds, work, stream, herm);
+}
+
+static cfd_status project_n(bool dw, double2 *X, int64_t ldx, int64_t n_rows, int n_in, const double2 *M,
+                            int64_t ldm, int n_out, double *work, cudaStream_t stream) {
+    return dw ? project_inplace_dw(X, ldx, n_rows, n_in, M, ldm, n_out, work, stream)
+              : project_inplace(X, ldx, n_rows, n_in, M, ldm, n_out, work, stream);
+}
+
 // One SVQB pass (Stathopoulos & Wu 2002): S = X^H X, D = diag(S)^{-1/2},
 // D S D = Q Theta Q^H, X <- X D Q Theta^{-1/2} with Theta clamped below at
-// tau max(Theta).
+// tau max(Theta).  dw: the Gram and the projection in double-word arithmetic.
 cfd_status svqb_pass(double2 *X, int64_t ldx, int64_t N, int n, double tau, void *work, size_t work_bytes,
-                     int *rank_dev, cudaStream_t stream) {
+                     int *rank_dev, cudaStream_t stream, bool dw) {
     Carve c(work, work_bytes);
     double2 *S = c.take<double2>((size_t)2 * n * n);
     double2 *Q = c.take<double2>((size_t)n * n);
@@ -70,7 +84,7 @@ cfd_status svqb_pass(double2 *X, int64_t ldx, int64_t N, int n, double tau, void
     size_t ew_bytes = eigh_workspace(n);
     void *ew = c.take<char>(ew_bytes);
     if (!c.fits()) return fail(CFD_ERR_OOM, "orthogonalisation workspace too small");
-    CFD_TRY(gram(X, ldx, n, X, ldx, n, N, S, n, gw, stream, true));
+    CFD_TRY(gram_n(dw, X, ldx, n, X, ldx, n, N, S, n, gw, stream, true));
     k_svqb_scale<<<(n * n + 255) / 256, 256, 0, stream>>>(S, n, d);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
@@ -78,7 +92,7 @@ cfd_status svqb_pass(double2 *X, int64_t ldx, int64_t N, int n, double tau, void
     k_svqb_coeff<<<(n * n + 255) / 256, 256, 0, stream>>>(Q, theta, d, n, tau, M, rank_dev ? rank_dev : rank);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
-    CFD_TRY(project_inplace(X, ldx, N, n, M, n, n, pw, stream));
+    CFD_TRY(project_n(dw, X, ldx, N, n, M, n, n, pw, stream));
     return CFD_OK;
 }
 
@@ -93,7 +107,7 @@ cfd_status check_c128_block(const cfd_block &X) {
 size_t orthogonalize_workspace(int64_t N, int n) { return svqb_workspace(N, n); }
 
 cfd_status orthogonalize_impl(const cfd_block &X, double tol, int *rank_host, int *rank_dev, void *work,
-                              size_t work_bytes, cudaStream_t stream) {
+                              size_t work_bytes, cudaStream_t stream, bool dw) {
     CFD_TRY(check_c128_block(X));
     if (!work) return fail(CFD_ERR_ARG, "work is NULL");
     if (work_bytes < orthogonalize_workspace(X.n_rows, X.n_cols))
@@ -104,8 +118,8 @@ cfd_status orthogonalize_impl(const cfd_block &X, double tol, int *rank_host, in
     int *r1 = c.take<int>(64);
     size_t rest = work_bytes - c.off;
     char *w2 = static_cast<char *>(work) + c.off;
-    CFD_TRY(svqb_pass(Xp, X.ld, X.n_rows, X.n_cols, tau, w2, rest, rank_dev ? rank_dev : r1, stream));
-    CFD_TRY(svqb_pass(Xp, X.ld, X.n_rows, X.n_cols, tau, w2, rest, nullptr, stream));
+    CFD_TRY(svqb_pass(Xp, X.ld, X.n_rows, X.n_cols, tau, w2, rest, rank_dev ? rank_dev : r1, stream, dw));
+    CFD_TRY(svqb_pass(Xp, X.ld, X.n_rows, X.n_cols, tau, w2, rest, nullptr, stream, dw));
     if (rank_host) {
         CFD_CUDA(cudaMemcpyAsync(rank_host, rank_dev ? rank_dev : r1, sizeof(int), cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaStreamSynchronize(stream));
@@ -229,7 +243,8 @@ size_t orth_rr_workspace(int64_t N, int n) {
 }
 
 cfd_status orth_rr_impl(const cfd_matrix *H, const cfd_block &X, double tol, int *rank_dev, double *evals,
-                        double *resid, void *work, size_t work_bytes, cudaEvent_t e_mid, cudaStream_t stream) {
+                        double *resid, void *work, size_t work_bytes, cudaEvent_t e_mid, cudaStream_t stream,
+                        bool dw) {
     CFD_TRY(check_matrix(H));
     CFD_TRY(check_c128_block(X));
     if (H->prec != CFD_C128) return fail(CFD_ERR_ARG, "Rayleigh-Ritz needs the complex-double matrix");
@@ -262,13 +277,13 @@ cfd_status orth_rr_impl(const cfd_matrix *H, const cfd_block &X, double tol, int
     double *rw = reinterpret_cast<double *>(c.take<char>(resid_workspace(n)));
     double2 *Xp = static_cast<double2 *>(X.ptr);
     // first pass: X1 = X0 M1
-    CFD_TRY(svqb_pass(Xp, X.ld, N, n, tau, sw, svqb_bytes, rank_dev ? rank_dev : r1, stream));
+    CFD_TRY(svqb_pass(Xp, X.ld, N, n, tau, sw, svqb_bytes, rank_dev ? rank_dev : r1, stream, dw));
     if (e_mid) CFD_CUDA(cudaEventRecord(e_mid, stream));
     // Z1 = H X1, S2 = X1^H X1, G1 = X1^H Z1
     CFD_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), stream));
     CFD_TRY(spmmv_block(H, Xp, X.ld, Z, n, n, partial, ticket, nullptr, stream));
-    CFD_TRY(gram(Xp, X.ld, n, Xp, X.ld, n, N, S, n, gw, stream, true));
-    CFD_TRY(gram(Xp, X.ld, n, Z, n, n, N, G1, n, gw, stream, true));
+    CFD_TRY(gram_n(dw, Xp, X.ld, n, Xp, X.ld, n, N, S, n, gw, stream, true));
+    CFD_TRY(gram_n(dw, Xp, X.ld, n, Z, n, n, N, G1, n, gw, stream, true));
     // second pass's coefficients M2 = D Q Theta^{-1/2} from S2
     k_svqb_scale<<<(n * n + 255) / 256, 256, 0, stream>>>(S, n, d);
     CFD_COUNT_LAUNCH();
@@ -283,8 +298,8 @@ cfd_status orth_rr_impl(const cfd_matrix *H, const cfd_block &X, double tol, int
     CFD_TRY(eigh(G, n, n, evals, Y, n, ew, ewb, stream, nullptr));
     // W = M2 Y; X <- X1 W, Z <- Z1 W; residual norms
     CFD_TRY(project_inplace(M, n, n, n, Y, n, n, pw, stream));
-    CFD_TRY(project_inplace(Xp, X.ld, N, n, M, n, n, pw, stream));
-    CFD_TRY(project_inplace(Z, n, N, n, M, n, n, pw, stream));
+    CFD_TRY(project_n(dw, Xp, X.ld, N, n, M, n, n, pw, stream));
+    CFD_TRY(project_n(dw, Z, n, N, n, M, n, n, pw, stream));
     if (resid) CFD_TRY(resid_norms(Z, n, Xp, X.ld, evals, n, N, resid, rw, stream));
     return CFD_OK;
 }
@@ -299,15 +314,21 @@ size_t cfd_gram_workspace(int64_t N, int n_x, int n_y) { return gram_workspace(N
 
 cfd_status cfd_block_gram(cfd_block X, cfd_block Y, void *S, int64_t lds, void *work, size_t work_bytes,
                           cudaStream_t stream) {
+    return cfd_block_gram_ex(X, Y, S, lds, work, work_bytes, 0, stream);
+}
+
+cfd_status cfd_block_gram_ex(cfd_block X, cfd_block Y, void *S, int64_t lds, void *work, size_t work_bytes,
+                             int arith, cudaStream_t stream) {
     clear_error();
+    if (arith != 0 && arith != 1) return fail(CFD_ERR_ARG, "arith=%d not in {0, 1}", arith);
     CFD_TRY(check_c128_block(X));
     CFD_TRY(check_c128_block(Y));
     if (X.n_rows != Y.n_rows) return fail(CFD_ERR_ARG, "blocks differ in rows");
     if (!S || lds < Y.n_cols) return fail(CFD_ERR_ARG, "S is NULL or lds < n_y");
     if (!work || work_bytes < gram_workspace(X.n_rows, X.n_cols, Y.n_cols))
         return fail(CFD_ERR_OOM, "Gram workspace too small");
-    return gram(static_cast<const double2 *>(X.ptr), X.ld, X.n_cols, static_cast<const double2 *>(Y.ptr), Y.ld,
-                Y.n_cols, X.n_rows, static_cast<double2 *>(S), lds, static_cast<double *>(work), stream);
+    return gram_n(arith == 1, static_cast<const double2 *>(X.ptr), X.ld, X.n_cols, static_cast<const double2 *>(Y.ptr), Y.ld,
+                Y.n_cols, X.n_rows, static_cast<double2 *>(S), lds, static_cast<double *>(work), stream, false);
 }
 
 size_t cfd_eigh_workspace(int n) { return n > 0 ? eigh_workspace(n) : 0; }
@@ -328,7 +349,14 @@ size_t cfd_orthogonalize_workspace(int64_t N, int n_s) {
 cfd_status cfd_orthogonalize(cfd_block X, double tol, int *rank, void *work, size_t work_bytes,
                              cudaStream_t stream) {
     clear_error();
-    return orthogonalize_impl(X, tol, rank, nullptr, work, work_bytes, stream);
+    return orthogonalize_impl(X, tol, rank, nullptr, work, work_bytes, stream, false);
+}
+
+cfd_status cfd_orthogonalize_ex(cfd_block X, double tol, int *rank, void *work, size_t work_bytes, int arith,
+                                cudaStream_t stream) {
+    clear_error();
+    if (arith != 0 && arith != 1) return fail(CFD_ERR_ARG, "arith=%d not in {0, 1}", arith);
+    return orthogonalize_impl(X, tol, rank, nullptr, work, work_bytes, stream, arith == 1);
 }
 
 size_t cfd_rayleigh_ritz_workspace(int64_t N, int n_s) { return (N > 0 && n_s > 0) ? rr_workspace(N, n_s) : 0; }

@@ -13,11 +13,12 @@ namespace cfd {
 
 size_t orthogonalize_workspace(int64_t N, int n);
 cfd_status orthogonalize_impl(const cfd_block &X, double tol, int *rank_host, int *rank_dev, void *work,
-                              size_t work_bytes, cudaStream_t stream);
+                              size_t work_bytes, cudaStream_t stream, bool dw);
 size_t rr_workspace(int64_t N, int n);
 size_t orth_rr_workspace(int64_t N, int n);
 cfd_status orth_rr_impl(const cfd_matrix *H, const cfd_block &X, double tol, int *rank_dev, double *evals,
-                        double *resid, void *work, size_t work_bytes, cudaEvent_t e_mid, cudaStream_t stream);
+                        double *resid, void *work, size_t work_bytes, cudaEvent_t e_mid, cudaStream_t stream,
+                        bool dw);
 cfd_status rayleigh_ritz_impl(const cfd_matrix *H, const cfd_block &X, double *evals, double *resid, void *work,
                               size_t work_bytes, cudaStream_t stream);
 size_t bounds_workspace(int64_t N, int steps);
@@ -72,7 +73,8 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
     if (p->policy < CFD_POLICY_FP64 || p->policy > CFD_POLICY_MIXED_DW)
         return fail(CFD_ERR_ARG, "unknown policy %d", p->policy);
     const bool mixed = p->policy == CFD_POLICY_MIXED || p->policy == CFD_POLICY_MIXED_DW;
-    // complex-double filter applications in double-word arithmetic
+    // complex-double filter applications, and the Gram matrices and
+    // projections of SVQB and Rayleigh-Ritz, in double-word arithmetic
     const bool dw = p->policy == CFD_POLICY_FP64_DW || p->policy == CFD_POLICY_MIXED_DW;
     if (mixed) {
         if (!H_low) return fail(CFD_ERR_ARG, "mixed policy needs the complex-float matrix H_low");
@@ -134,7 +136,7 @@ cfd_status cfd_solve(const cfd_matrix *H, const cfd_matrix *H_low, const cfd_sol
         // SVQB's first pass (t_orth), then its second pass folded into
         // Rayleigh-Ritz (t_rr)
         CFD_TRY(orth_rr_impl(H, X, 1e-14, reinterpret_cast<int *>(small + 8), ev_dev, rs_dev, scratch, scratch_bytes,
-                             e2, stream));
+                             e2, stream, dw));
         cudaEventRecord(e3, stream);
         CFD_CUDA(cudaMemcpyAsync(evals, ev_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));
         CFD_CUDA(cudaMemcpyAsync(resid, rs_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));

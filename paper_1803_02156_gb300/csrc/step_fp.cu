@@ -341,7 +341,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
         };
         const float4 w_step = A.chunk_rid ? make_float4(0.f, 0.f, 0.f, 0.f) : weight(A.gc[A.p]);
         // chunk c into stage s from its descriptor (lane l holds word l)
-        auto issue = [&](int64_t c, int s, int2 d) {
+        auto issue = [&](int64_t c, int s, int2 d, double wd) {
             unsigned char *st = smem_raw + (size_t)s * L.stage;
             const int cl = __shfl_sync(0xffffffffu, d.x, 0);
             const int nr = __shfl_sync(0xffffffffu, d.y, 0);
@@ -365,11 +365,10 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
             off -= g.y;
             const uint32_t bytes = nslot * (uint32_t)sizeof(V) + (uint32_t)own * RB * (XST ? 2u : 1u) +
                                    (nr >= 0 ? nslot * 2u + (uint32_t)tot * RB : 0u) + tx_extra;
-            const int rid = __shfl_sync(0xffffffffu, d.x, 3);
             if (lane == 0) {
                 s_info[s] = make_int4(cl, nr, own_off, own);
                 // the step's weight g_p c_p (in a batch, that of the chunk's realisation)
-                s_w[s] = A.chunk_rid ? weight(__ldg(A.rcoef + (int64_t)rid * A.rcoef_ld + 2 + A.p)) : w_step;
+                s_w[s] = A.chunk_rid ? weight(wd) : w_step;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (lane == 0) mbar_expect_tx(&full[s], bytes);
@@ -382,11 +381,22 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                 tma_load_1d(st + L.rows + (uint32_t)off * RB, vin + (int64_t)g.x * NB, (uint32_t)g.y * RB, &full[s]);
         };
         bool failed = false;
-        // descriptors one chunk ahead, so their load latency is off the issue path
-        int2 dnext = first < n_chunks ? __ldg(F.desc + first * 32 + lane) : make_int2(0, 0);
+        // descriptors two chunks ahead and (in a batch) each chunk's weight
+        // one chunk ahead, so no load latency sits on the issue path
+        auto ld_desc = [&](int64_t c) { return c < n_chunks ? __ldg(F.desc + c * 32 + lane) : make_int2(0, 0); };
+        auto ld_weight = [&](int64_t c, int2 d) {
+            if (!A.chunk_rid || c >= n_chunks) return 0.0;
+            const int rid = __shfl_sync(0xffffffffu, d.x, 3);
+            return __ldg(A.rcoef + (int64_t)rid * A.rcoef_ld + 2 + A.p);
+        };
+        int2 d1 = ld_desc(first), d2 = ld_desc(first + stride);
+        double w1 = ld_weight(first, d1);
         for (int64_t c = first; c < n_chunks; c += stride, ++issued) {
-            const int2 d = dnext;
-            if (c + stride < n_chunks) dnext = __ldg(F.desc + (c + stride) * 32 + lane);
+            const int2 d = d1;
+            const double wd = w1;
+            d1 = d2;
+            d2 = ld_desc(c + 2 * stride);
+            w1 = ld_weight(c + stride, d1);
             const int s = issued % S;
             if (issued >= S) {
                 const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)((issued / S - 1) & 1), limit);
@@ -395,7 +405,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                     break;
                 }
             }
-            issue(c, s, d);
+            issue(c, s, d, wd);
         }
         if (failed && lane == 0) {
             *abort_flag = 1;
@@ -671,6 +681,11 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
 #ifndef CFD_FP_DW_STAGES
 #define CFD_FP_DW_STAGES 2
 #endif
+// Chunks per SM below which the filter keeps the gathered steps (unless the
+// caller asks for the footprint steps explicitly).
+#ifndef CFD_FP_MIN_CHUNKS_PER_SM
+#define CFD_FP_MIN_CHUNKS_PER_SM 16
+#endif
 // Vectors per thread, and consumer warps of the CTA (one CTA per SM, plus
 // the producer warp; 0: one row per thread and chunk, n_b / vpt warps).
 #ifndef CFD_FP_C64_VPT
@@ -818,12 +833,15 @@ size_t footprint_bytes(int64_t N) {
     return round_up((size_t)kMaxRowSlots * (size_t)(N + 127) * 2, 256) + round_up((size_t)n_chunks * 256, 256);
 }
 
-int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw) {
+int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw, bool any_size) {
     const int slots_bound = (H->flags >> CFD_MATRIX_SLOTS_SHIFT) & 0xff;
     (void)vpt;
     if (nb != FP_NB || H->C != FP_C || H->perm || !(H->flags & CFD_MATRIX_PACKED)) return 0;
     if (slots_bound < 1 || slots_bound * FP_C + FP_C > FP_KEYS) return 0;
     if (H->n_rows >= (int64_t)INT_MAX) return 0;
+    // one CTA per SM ramps its pipeline up per launch: below a few chunks per
+    // SM the gathered steps (several CTAs per SM) are faster
+    if (!any_size && H->n_chunks < (int64_t)CFD_FP_MIN_CHUNKS_PER_SM * sm_count()) return 0;
     if (dw ? H->prec != CFD_C128 : H->prec != CFD_C64) return 0;
     const int cap = dw ? fp_rows_cap_t<FPM_DW>(slots_bound * FP_C) : fp_rows_cap_t<FPM_C64>(slots_bound * FP_C);
     return std::min(cap, 65535);

@@ -214,3 +214,90 @@ def test_solve_argument_errors(b):
     with pytest.raises(b.CfdError) as e:
         b.cfd_solve(H, X, -0.5, 0.5, 20, 32, max_iter=1, lmin=-9, lmax=9, n_t=16)
     assert e.value.status == 6
+
+
+# ----------------------------------------------- double-word Gram and SVQB --
+# Every double split once into hi + lo floats, every multiply-add a
+# double-word one: each term accurate to a few units of 2^-48 (against 2^-53
+# for fp64), so the bars are those of the fp64 tests with 2^5 more rounding.
+
+@pytest.mark.parametrize("N,nx,ny", [(2048, 32, 32), (5001, 24, 40), (100003, 128, 128), (77, 8, 16),
+                                     (300, 256, 256), (20000, 256, 200)])
+def test_gram_dw_vs_numpy(b, N, nx, ny):
+    X = inputs.gaussian_block(N, nx, seed=1)
+    Y = inputs.gaussian_block(N, ny, seed=2)
+    S = b.cfd_block_gram(_cuda(X), _cuda(Y), arith=1).cpu().numpy()
+    ref = X.conj().T @ Y
+    assert np.max(np.abs(S - ref)) < 32 * 1e-13 * np.sqrt(N) * 4
+
+
+def test_gram_dw_hermitian_and_strided(b):
+    """X^H X of a column window (ld > n): the Hermitian path (tiles below the
+    diagonal mirrored by the fold) against numpy, and exactly Hermitian."""
+    X = inputs.gaussian_block(30011, 256, seed=4)
+    Xg = _cuda(X)
+    S = b.cfd_block_gram(Xg[:, 0:192], Xg[:, 0:192], arith=1).cpu().numpy()
+    ref = X[:, :192].conj().T @ X[:, :192]
+    assert np.max(np.abs(S - ref)) < 32 * 1e-13 * np.sqrt(30011) * 4
+    S2 = b.cfd_block_gram(Xg[:, 16:48], Xg[:, 8:24], arith=1).cpu().numpy()
+    assert np.max(np.abs(S2 - X[:, 16:48].conj().T @ X[:, 8:24])) < 1e-10
+
+
+@pytest.mark.parametrize("N,n", [(4096, 32), (20000, 128), (3001, 256), (100003, 256)])
+def test_orthogonalize_dw_random(b, N, n):
+    """SVQB with double-word Grams and projections: orthonormal to 1e-12 and
+    the same span as the input."""
+    X = inputs.gaussian_block(N, n, seed=7)
+    Xg = _cuda(X)
+    rank = b.cfd_orthogonalize(Xg, arith=1)
+    Q = Xg.cpu().numpy()
+    assert rank == n
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(n)) <= 1e-12
+    P = Q @ (Q.conj().T @ X)
+    assert np.linalg.norm(X - P) <= 1e-11 * np.linalg.norm(X)
+
+
+def test_orthogonalize_dw_filtered_block(b):
+    """The ill-conditioned filter output (8x8x8, n_p = 200) through the
+    double-word SVQB: orthonormal, leading directions of the oracle's basis kept."""
+    H = oracle.topi_csr(8, 8, 8)
+    X = inputs.gaussian_block(H.N, 32, seed=2)
+    Y, _ = oracle.chebfd_filter(H, -8.6, 8.6, -0.7, 0.7, 200, X, 32)
+    Yg = _cuda(Y)
+    b.cfd_orthogonalize(Yg, arith=1)
+    Q = Yg.cpu().numpy()
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(32)) <= 1e-12
+    Qo = oracle.mgs2(Y)
+    s = np.linalg.svd(Qo[:, :16].conj().T @ Q, compute_uv=False)
+    assert np.min(s) > 1 - 1e-8
+
+
+def test_dense_dw_option_rejected(b):
+    X = _cuda(inputs.gaussian_block(100, 8, seed=1))
+    with pytest.raises(b.CfdError) as e:
+        b.cfd_block_gram(X, X, arith=2)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("policy", ["fp64_dw", "mixed_dw"])
+def test_solve_dw_policies(b, policy):
+    """The double-word policies (filter, SVQB and Rayleigh-Ritz in double-word
+    arithmetic; mixed: complex-float filter first) on 8x8x8: converged
+    in-window eigenvalues equal dense eigh's to 1e-10, residuals <= 1e-10,
+    the returned block orthonormal."""
+    import torch
+    ev, delta, k = _small_truth()
+    w = workloads.SMALL
+    H = b.cfd_build_matrix(b.topi_params(*w.lattice), 32, 1, "c128p")
+    Hl = b.cfd_build_matrix(b.topi_params(*w.lattice), 32, 1, "c64p")
+    X = torch.empty(w.N, w.n_s, dtype=torch.complex128, device="cuda")
+    pol = b.CFD_POLICY_FP64_DW if policy == "fp64_dw" else b.CFD_POLICY_MIXED_DW
+    th, rs, res = b.cfd_solve(H, X, -delta, delta, w.n_p, w.n_b, H_low=Hl if policy == "mixed_dw" else None,
+                              policy=pol, n_t=k, tol=1e-10, seed=2)
+    inside = (th >= -delta) & (th <= delta) & (rs <= 1e-10)
+    exact = np.sort(ev[np.abs(ev) < delta])
+    assert res.n_conv == k == inside.sum()
+    assert np.max(np.abs(np.sort(th[inside]) - exact)) < 1e-10
+    assert np.max(rs[inside]) <= 1e-10
+    Q = X.cpu().numpy()
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(w.n_s)) < 1e-11

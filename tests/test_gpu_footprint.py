@@ -16,6 +16,7 @@ from paper_1803_02156_gb300 import inputs, workloads
 pytestmark = pytest.mark.gpu
 
 MOM_TOL = {"c64p": 1e-5, "c128p": 1e-13}
+FORCE = 65535      # footprint steps at any matrix size, no row cap below the stage's own
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +58,7 @@ def test_footprint_equals_gathered(b, prec, L, per):
     """Staged footprints on lattices with ragged last chunks (3x3x3: N = 108),
     chunks spanning several x-lines and open boundaries: bit for bit."""
     import torch
-    Xf, Xg, muf, mug = _pair(b, L, prec, 64, 30, (-0.6, 0.4), 0, per=per)
+    Xf, Xg, muf, mug = _pair(b, L, prec, 64, 30, (-0.6, 0.4), FORCE, per=per)
     assert torch.equal(Xf, Xg)
     _mom_close(muf, mug, prec)
 
@@ -79,7 +80,7 @@ def test_footprint_mixed_precision_block(b):
     """The complex-float matrix on a complex-double block (narrowed per block,
     the mixed policy's filter): bit for bit."""
     import torch
-    Xf, Xg, muf, mug = _pair(b, (8, 8, 8), "c64p", 64, 25, (-0.7, 0.7), 0, mixed=True)
+    Xf, Xg, muf, mug = _pair(b, (8, 8, 8), "c64p", 64, 25, (-0.7, 0.7), FORCE, mixed=True)
     assert Xf.dtype == torch.complex128
     assert torch.equal(Xf, Xg)
     _mom_close(muf, mug, "c64p")
@@ -96,7 +97,7 @@ def test_footprint_parity_small_config(b, prec, tol):
     X = inputs.gaussian_block(ref.N, 64, seed=2)
     Xg = torch.from_numpy(X).cuda()
     mu = b.cfd_filter_ex(H, -8.6, 8.6, -0.7, 0.7, w.n_p, Xg, 32, moments=True,
-                         arith=1 if prec == "c128p" else 0, footprint=0)
+                         arith=1 if prec == "c128p" else 0, footprint=FORCE)
     torch.cuda.synchronize()
     Y, dots = oracle.chebfd_filter(ref, -8.6, 8.6, -0.7, 0.7, w.n_p, X, 32)
     err = np.linalg.norm(Xg.cpu().numpy() - Y) / np.linalg.norm(Y)
@@ -122,7 +123,7 @@ def test_footprint_graph_replay(b, prec):
     """Captured as a CUDA graph (footprint build included) and replayed."""
     import torch
     for _ in range(2):
-        Xf, Xg, muf, mug = _pair(b, (8, 8, 6), prec, 32, 15, (-0.5, 0.5), 0, graph=1)
+        Xf, Xg, muf, mug = _pair(b, (8, 8, 6), prec, 32, 15, (-0.5, 0.5), FORCE, graph=1)
         assert torch.equal(Xf, Xg)
         _mom_close(muf, mug, prec)
 
@@ -139,7 +140,7 @@ def test_footprint_wait_timeout_reported(b, prec):
     X = torch.from_numpy(inputs.gaussian_block(H.N, 32, seed=6)).to(dt).cuda()
     pw = "c128" if prec == "c128p" else "c64"
     work = torch.empty(b.cfd_filter_workspace(H.N, 32, 32, 10, pw, pw), dtype=torch.uint8, device="cuda")
-    b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 10, X, 32, arith=arith, staged=2, footprint=0, work=work)
+    b.cfd_filter_ex(H, -8.6, 8.6, -0.5, 0.5, 10, X, 32, arith=arith, staged=2, footprint=FORCE, work=work)
     with pytest.raises(b.CfdError) as e:
         b.cfd_workspace_status(work)
     assert e.value.status == 5
@@ -160,12 +161,12 @@ def test_footprint_option_rejected(b):
 
 @pytest.mark.parametrize("prec", ["c64p", "c128p"])
 def test_footprint_batched_equals_per_realisation(b, prec):
-    """The batched filter (block-diagonal matrix of five uneven lattices, each
-    chunk's weight taken from its realisation) with the footprint steps: per
-    realisation bit for bit cfd_filter on that lattice alone with the
-    gathered steps."""
+    """The batched filter (block-diagonal matrix of five uneven lattices,
+    about 3100 chunks, enough for the default to take the footprint steps;
+    each chunk's weight taken from its realisation): per realisation bit for
+    bit cfd_filter on that lattice alone with the gathered steps."""
     import torch
-    lattices = [(5, 6, 3, 11), (7, 3, 4, 12), (4, 4, 5, 13), (3, 5, 2, 14), (6, 6, 6, 15)]
+    lattices = [(24, 20, 12, 11), (20, 22, 10, 12), (18, 16, 14, 13), (26, 18, 11, 14), (22, 22, 12, 15)]
     arith = 1 if prec == "c128p" else 0
     dt = torch.complex128 if prec == "c128p" else torch.complex64
     B = b.cfd_build_batch([b.topi_params(nx, ny, nz, seed=s) for (nx, ny, nz, s) in lattices], 32, 1, prec)
