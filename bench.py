@@ -107,7 +107,7 @@ def parse():
     ap.add_argument("--tte-workload", default=None, choices=sorted(workloads.ALL),
                     help="the workload whose time to eigenpairs is measured (default: the 128x128x64 one)")
     ap.add_argument("--mode", default="filter",
-                    choices=["filter", "iteration", "batch", "fusion", "host", "sweep", "tte", "peaks", "kernel",
+                    choices=["filter", "iteration", "batch", "fusion", "host", "sweep", "tte", "peaks", "dense", "kernel",
                              "dist"],
                     help="filter: n_b = 32 blocks of the 200x200x100 lattice at n_p = 100, plus time to "
                          "eigenpairs (default); iteration: the 64x64x32 ChebFD iteration (filter, SVQB, "
@@ -128,6 +128,7 @@ def parse():
     ap.add_argument("--gather", type=int, default=0, help="kernel mode: cfd_filter_opts.gather")
     ap.add_argument("--vpt", type=int, default=0, help="kernel mode: vectors per thread (0: default)")
     ap.add_argument("--no-moments", action="store_true", help="kernel mode: filter without moments")
+    ap.add_argument("--dense-n", type=int, default=4194304, help="dense mode: rows of the N x 256 block")
     ap.add_argument("--footprint", type=int, default=0,
                     help="cfd_filter_opts.footprint: 0 footprint-staged general steps where they apply, -1 never")
     ap.add_argument("--arith", default="dw", choices=["native", "dw"],
@@ -1240,6 +1241,54 @@ def run_peaks(a):
                       "nominal_fp64_gflops": round(FP64_PEAK_GFLOPS, 1), "results": out}))
 
 
+def run_dense(a):
+    """The dense kernels of SVQB and Rayleigh-Ritz on an N x n complex-double
+    block (N = --dense-n, n = 256, the 128x128x64 solve's shape by default):
+    the Gram X^H Y (cfd_block_gram_ex) and one SVQB orthonormalisation (two
+    Hermitian Grams and two in-place projections, cfd_orthogonalize_ex), in
+    fp64 on the FP64 tensor cores and in double-word arithmetic on the fp32
+    pipe.  GFLOP/s count 8 N n^2 real flops per Gram (the full product) and
+    per projection, so SVQB's two passes count 4 x 8 N n^2 (its Hermitian
+    Grams compute about half of that); CUDA events, median of --steps after
+    --warmup."""
+    import torch
+    from paper_1803_02156_gb300 import binding as b, inputs
+    torch.cuda.set_device(0)
+    N, n = a.dense_n, 256
+    X = inputs.gaussian_block_device(N, n, seed=5)
+    Y = inputs.gaussian_block_device(N, n, seed=6)
+    out = {}
+    for arith, name in ((0, "fp64_tensor"), (1, "double_word")):
+        def timed(fn):
+            ts = []
+            for r in range(a.warmup + a.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                if r >= a.warmup:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+            return statistics.median(ts)
+        tg = timed(lambda: b.cfd_block_gram(X, Y, arith=arith))
+        Z = X.clone()
+
+        def orth():
+            Z.copy_(X)
+            b.cfd_orthogonalize(Z, arith=arith)
+        t0 = timed(lambda: Z.copy_(X))
+        to = timed(orth) - t0
+        flops = 8.0 * N * n * n
+        out[name] = {"gram_s": round(tg, 5), "gram_gflops": round(flops / tg / 1e9, 1),
+                     "svqb_s": round(to, 5),
+                     "svqb_gflops": round(4 * flops / to / 1e9, 1)}
+    out["speedup_gram"] = round(out["fp64_tensor"]["gram_s"] / out["double_word"]["gram_s"], 3)
+    out["speedup_svqb"] = round(out["fp64_tensor"]["svqb_s"] / out["double_word"]["svqb_s"], 3)
+    print(json.dumps({"metric": "dense SVQB / Rayleigh-Ritz kernels", "unit": "s", "n_gpus": 1, "steps": a.steps,
+                      "warmup": a.warmup, "config": {"N": N, "n": n, "block": "complex double, Gaussian"},
+                      "results": out}))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -1256,6 +1305,8 @@ def main():
         run_tte(a)
     elif a.mode == "peaks":
         run_peaks(a)
+    elif a.mode == "dense":
+        run_dense(a)
     elif a.mode == "kernel":
         run_kernel(a)
     elif a.mode == "dist":
