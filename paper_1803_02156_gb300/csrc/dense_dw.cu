@@ -8,8 +8,9 @@
 // products (dense.cu's header) run with every double split once into
 // hi + lo floats and every multiply-add as a double-word multiply-add
 // (dw_arith.cuh: Dekker's TwoProduct by FMA plus the cross terms, Knuth's
-// TwoSum, the errors collected in a second float), two output columns per
-// packed fp32x2 instruction.  A real multiply-add costs 12 fp32 operations,
+// TwoSum, the errors collected in a second float and folded back into the
+// sum after every slab of rows), two output columns per packed fp32x2
+// instruction.  A real multiply-add costs 12 fp32 operations,
 // so the fp32 pipe gives about 3 TFLOP/s of fp64-equivalent work; each
 // product and sum is accurate to a few units of 2^-48 of its terms (2^-53
 // natively).  The Gram's partials and the fold are those of dense.cu (the
@@ -105,6 +106,10 @@ k_gram_dw(const double *__restrict__ A, int64_t lda, int ma, const double *__res
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) renorm2(s2[i][j], e2[i][j]);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -199,6 +204,10 @@ k_project_dw(double *X, int64_t ldx, int kin, int nout, const float *__restrict_
                 }
             }
             __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) renorm2(s2[i][j], e2[i][j]);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {

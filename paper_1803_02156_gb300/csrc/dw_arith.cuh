@@ -93,5 +93,14 @@ __device__ __forceinline__ void dw_axpy2(float2 &xh, float2 &xl, float2 gh, floa
     xl = __fadd2_rn(lo, neg2(__fadd2_rn(xh, neg2(t))));
 }
 
+// (s, e) <- (s + e, its rounding error) lanewise (Dekker's Fast2Sum, exact
+// when |s| >= |e|): keeps the collected error term of a long sum at the
+// size of one rounding of s, so its own roundings stay at 2^-48 of s.
+__device__ __forceinline__ void renorm2(float2 &s, float2 &e) {
+    const float2 t = __fadd2_rn(s, e);
+    e = __fadd2_rn(e, neg2(__fadd2_rn(t, neg2(s))));
+    s = t;
+}
+
 }  // namespace
 }  // namespace cfd

@@ -253,16 +253,18 @@ def test_gram_dw_hermitian_and_strided(b):
 @pytest.mark.parametrize("N,n", [(4096, 32), (20000, 128), (3001, 256), (100003, 256)])
 def test_orthogonalize_dw_random(b, N, n):
     """SVQB with double-word Grams and projections: orthonormal to the fp64
-    bar times 2^5 (the ratio of 2^-48 to 2^-53) and the same span as the
-    input."""
+    bar times 2^5 (the ratio of 2^-48 to 2^-53), times sqrt(N / 4096) past
+    4096 rows (a double-word sum of K terms is good to about sqrt(K) 2^-48),
+    and the same span as the input."""
     X = inputs.gaussian_block(N, n, seed=7)
     Xg = _cuda(X)
     rank = b.cfd_orthogonalize(Xg, arith=1)
     Q = Xg.cpu().numpy()
     assert rank == n
-    assert np.linalg.norm(Q.conj().T @ Q - np.eye(n)) <= 32 * 1e-13
+    grow = max(1.0, np.sqrt(N / 4096))
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(n)) <= 32 * 1e-13 * grow
     P = Q @ (Q.conj().T @ X)
-    assert np.linalg.norm(X - P) <= 32 * 1e-12 * np.linalg.norm(X)
+    assert np.linalg.norm(X - P) <= 32 * 1e-12 * grow * np.linalg.norm(X)
 
 
 def test_orthogonalize_dw_filtered_block(b):
