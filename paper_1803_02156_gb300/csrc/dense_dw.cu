@@ -30,7 +30,7 @@ constexpr int GD_TM = 64;           // output tile (real) 64 rows x 128 columns
 constexpr int GD_TN = 128;
 constexpr int GD_KS = 16;           // rows per slab
 constexpr int GD_THREADS = 256;
-constexpr int GD_TARGET_CTAS = 152; // one wave of one CTA per SM on a 152-SM GB300
+constexpr int GD_TARGET_CTAS = 304; // two waves of one CTA per SM on a 152-SM GB300
 
 constexpr int PD_ROWS = 32;         // rows per CTA of the projection
 constexpr int PD_NT = 128;          // output columns per pass
@@ -70,18 +70,38 @@ k_gram_dw(const double *__restrict__ A, int64_t lda, int ma, const double *__res
 #pragma unroll
         for (int j = 0; j < 4; ++j) s2[i][j] = e2[i][j] = make_float2(0.f, 0.f);
 
-    for (int64_t k0 = k_begin; k0 < k_end; k0 += GD_KS) {
-        for (int e = threadIdx.x; e < GD_KS * GD_TM; e += GD_THREADS) {
-            const int r = e / GD_TM, c = e % GD_TM;
+    // the next slab's values are loaded into registers while the current
+    // slab is computed, then split into shared memory
+    constexpr int PA = GD_KS * GD_TM / GD_THREADS, PB = GD_KS * GD_TN / GD_THREADS;
+    double pa[PA], pb[PB];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int t = 0; t < PA; ++t) {
+            const int e = threadIdx.x + t * GD_THREADS, r = e / GD_TM, c = e % GD_TM;
             const int64_t k = k0 + r;
-            split_dw((k < k_end && m0 + c < ma) ? A[k * lda + m0 + c] : 0.0, Ah[r][c], Al[r][c]);
+            pa[t] = (k < k_end && m0 + c < ma) ? A[k * lda + m0 + c] : 0.0;
         }
-        for (int e = threadIdx.x; e < GD_KS * GD_TN; e += GD_THREADS) {
-            const int r = e / GD_TN, c = e % GD_TN;
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            const int e = threadIdx.x + t * GD_THREADS, r = e / GD_TN, c = e % GD_TN;
             const int64_t k = k0 + r;
-            split_dw((k < k_end && n0 + c < nb) ? B[k * ldb + n0 + c] : 0.0, Bh[r][c], Bl[r][c]);
+            pb[t] = (k < k_end && n0 + c < nb) ? B[k * ldb + n0 + c] : 0.0;
+        }
+    };
+    if (k_begin < k_end) load(k_begin);
+    for (int64_t k0 = k_begin; k0 < k_end; k0 += GD_KS) {
+#pragma unroll
+        for (int t = 0; t < PA; ++t) {
+            const int e = threadIdx.x + t * GD_THREADS;
+            split_dw(pa[t], Ah[e / GD_TM][e % GD_TM], Al[e / GD_TM][e % GD_TM]);
+        }
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+            const int e = threadIdx.x + t * GD_THREADS;
+            split_dw(pb[t], Bh[e / GD_TN][e % GD_TN], Bl[e / GD_TN][e % GD_TN]);
         }
         __syncthreads();
+        if (k0 + GD_KS < k_end) load(k0 + GD_KS);
 #pragma unroll 2
         for (int kk = 0; kk < GD_KS; ++kk) {
             const float4 x = *reinterpret_cast<const float4 *>(&Ah[kk][4 * ty]);
