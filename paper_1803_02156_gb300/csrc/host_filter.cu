@@ -108,6 +108,15 @@ extern "C" size_t cfd_filter_host_workspace(int64_t N, int n_s, int n_b, int n_p
 #ifndef CFD_HOST_BLOCKED_KERNEL
 #define CFD_HOST_BLOCKED_KERNEL 1
 #endif
+// Schedule of a block-after-block search space: 0 overlapped (block b + 1
+// comes in and b - 1 goes out on the copy stream while b is filtered), 1
+// serial (each block's DMA copies on the filter's own stream, before and
+// after its filter, at the link's full rate).  Next to the footprint-staged
+// steps the overlapped copies are starved to a few GB/s, so moving the
+// blocks while nothing else runs costs less.
+#ifndef CFD_HOST_SERIAL
+#define CFD_HOST_SERIAL 1
+#endif
 
 static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
                                    int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,
@@ -152,6 +161,22 @@ static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax
     const int n_blocks = X.n_cols / n_b;
     char *host = static_cast<char *>(X.ptr);
 
+    if (blocked && CFD_HOST_SERIAL) {
+        const size_t block_bytes = (size_t)N * width;
+        for (int b = 0; b < n_blocks; ++b) {
+            CFD_CUDA(cudaMemcpyAsync(dbuf[0], host + (size_t)b * block_bytes, block_bytes, cudaMemcpyHostToDevice,
+                                     stream));
+            cfd_block D = X;
+            D.ptr = dbuf[0];
+            D.ld = n_b;
+            D.n_cols = n_b;
+            CFD_TRY(filter_impl_opts(H, lmin, lmax, lam_l, lam_r, n_p, D, n_b, 0, 0, 0, 0, work, fws,
+                                     moments ? moments + (int64_t)b * n_b * 2 * n_p : nullptr, stream, 0, 0, arith));
+            CFD_CUDA(cudaMemcpyAsync(host + (size_t)b * block_bytes, dbuf[0], block_bytes, cudaMemcpyDeviceToHost,
+                                     stream));
+        }
+        return CFD_OK;
+    }
     CopyPipe cp;
     CFD_TRY(cp.create());
     // the copy stream starts after the work already queued on `stream`
