@@ -53,9 +53,7 @@ __device__ __forceinline__ float4 dw_scale(float4 v, float h) {
 //   general: V_new = P V_cur - V_prev;  X <- X + g_p V_new
 // with the moments' dots <vin, vin>, Re <w, vin>.  Arguments: those of the
 // native steps (StepArgs<double>); the block pointers hold double-words,
-// prep_val the double-word prepared values (per slot {hi, s hi, -lo, -s lo},
-// s = 1 in the real slots and -1 in the imaginary ones: the operands of the
-// slot's packed double-word multiply-add as they are used).
+// prep_val the double-word prepared values (float2 {hi, lo} per slot).
 // LAST: X is written back as complex double.  A row's X and own vin entries
 // are loaded after its row sum (loading them before holds their registers
 // across the gathers and costs a resident CTA: measured slower).
@@ -70,7 +68,7 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
     const int col_bytes = (int)round_up_dev((size_t)slots_cap * 4, 16);
     auto col_s = [&](int b) { return reinterpret_cast<int32_t *>(smem_raw + b * col_bytes); };
     auto val_s = [&](int b) {
-        return reinterpret_cast<float4 *>(smem_raw + 2 * col_bytes + (size_t)b * slots_cap * sizeof(float4));
+        return reinterpret_cast<float2 *>(smem_raw + 2 * col_bytes + (size_t)b * slots_cap * sizeof(float2));
     };
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -80,7 +78,7 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
     const int chunk_h = CH > 0 ? CH : 1 << log2C;
     const int64_t n_rows = A.H.n_rows;
     const int64_t n_chunks = (n_rows + chunk_h - 1) >> log2C;
-    const float4 *gval = reinterpret_cast<const float4 *>(A.prep_val);
+    const float2 *gval = reinterpret_cast<const float2 *>(A.prep_val);
     const float4 *vin = reinterpret_cast<const float4 *>(A.vin);
     float4 *wout = reinterpret_cast<float4 *>(A.w);
     float4 *xdw = reinterpret_cast<float4 *>(A.x);
@@ -120,10 +118,10 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
         const uint32_t nslot = (uint32_t)len << log2C;
         s_len[b] = cl;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&bar[b], nslot * (uint32_t)(4 + sizeof(float4)) + tx_extra);
+        mbar_expect_tx(&bar[b], nslot * (uint32_t)(4 + sizeof(float2)) + tx_extra);
         if (nslot) {
             tma_load_1d(col_s(b), A.H.col + base, nslot * 4u, &bar[b]);
-            tma_load_1d(val_s(b), gval + base, nslot * (uint32_t)sizeof(float4), &bar[b]);
+            tma_load_1d(val_s(b), gval + base, nslot * (uint32_t)sizeof(float2), &bar[b]);
         }
     };
 
@@ -148,7 +146,7 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
                 if (r >= n_rows) continue;
                 const int64_t i = A.H.perm ? (int64_t)__ldg(A.H.perm + r) : r;
                 const int32_t *colp = col_s(b) + rr;
-                const float4 *valp = val_s(b) + rr;
+                const float2 *valp = val_s(b) + rr;
                 // the row sum starts at -V_prev (general), -X (second) or 0:
                 // (s, e), lane 0 the real part, lane 1 the imaginary part
                 float4 u[VPT], xo[VPT];
@@ -176,11 +174,10 @@ k_cheb_step_dw(const StepArgs<double> A, int slots_cap) {
                 // the accumulator lanes swapped to (im, re) for the whole
                 // group: (im, re) += (h, -h) (v_re, v_im), i.e. i h v
                 auto madd = [&](int kk, bool imag, const float4 (&v)[VPT]) {
-                    (void)imag;    // the slot's sign is in its prepared value
-                    const float4 h = valp[kk << log2C];
-                    const float2 hh = make_float2(h.x, h.y);
+                    const float2 h = valp[kk << log2C];
+                    const float2 hh = make_float2(h.x, imag ? -h.x : h.x);
                     const float2 nhh = neg2(hh);
-                    const float2 nhl = make_float2(h.z, h.w);
+                    const float2 nhl = make_float2(-h.y, imag ? h.y : -h.y);
 #pragma unroll
                     for (int q = 0; q < VPT; ++q)
                         dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y), make_float2(v[q].z, v[q].w));
@@ -318,19 +315,16 @@ __global__ void k_dw_convert(double2 *p, int64_t ld, int64_t n_rows, int nb) {
     }
 }
 
-// Prepared values 2 alpha (H - beta) as double-words, one per packed slot in
-// H's SELL layout (the double-word form of k_prepare_values' output), stored
-// as the packed multiply-add uses them: {hi, s hi, -lo, -s lo} with s = 1 in
-// a chunk's real slots and -1 in its imaginary slots.
+// Prepared values 2 alpha (H - beta) as double-words {hi, lo}, one per packed
+// slot, in H's SELL layout (the double-word form of k_prepare_values' output).
 __global__ void k_prepare_values_dw(SellView<double> H, int64_t n_pos, double alpha, double beta,
-                                    const int32_t *chunk_rid, const double *rcoef, int64_t rcoef_ld, float4 *out) {
+                                    const int32_t *chunk_rid, const double *rcoef, int64_t rcoef_ld, float2 *out) {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_pos) return;
     const int64_t ch = r >> H.log2C;
     const int64_t base = H.chunk_ptr[ch] + (r & ((1 << H.log2C) - 1));
     const int cl = H.chunk_len[ch];
-    const int n_re = cl & 0xffff;
-    const int len = n_re + (cl >> 16);
+    const int len = (cl & 0xffff) + (cl >> 16);
     const int64_t i = r < H.n_rows ? (H.perm ? (int64_t)H.perm[r] : r) : -2;
     if (chunk_rid) {
         const double *rc = rcoef + (int64_t)chunk_rid[ch] * rcoef_ld;
@@ -343,8 +337,7 @@ __global__ void k_prepare_values_dw(SellView<double> H, int64_t n_pos, double al
         const double h = H.pval[s];
         const double v = H.col[s] == i ? a2 * (h - beta) : a2 * h;
         const float hi = __double2float_rn(v);
-        const float lo = __double2float_rn(v - (double)hi);
-        out[s] = k < n_re ? make_float4(hi, hi, -lo, -lo) : make_float4(hi, -hi, -lo, lo);
+        out[s] = make_float2(hi, __double2float_rn(v - (double)hi));
     }
 }
 
@@ -356,7 +349,7 @@ template <int NB, int VPT, int KIND, bool MOM, int CH, bool LAST>
 cfd_status launch_dw_t(const StepArgs<double> &A, int grid_cap, cudaStream_t stream) {
     const int slots_cap = A.H.slots_bound << A.H.log2C;
     if (slots_cap <= 0) return fail(CFD_ERR_ARG, "matrix has no slot bound; cannot stage");
-    const size_t smem = 2 * round_up((size_t)slots_cap * 4, 16) + round_up(2 * (size_t)slots_cap * sizeof(float4), 16);
+    const size_t smem = 2 * round_up((size_t)slots_cap * 4, 16) + round_up(2 * (size_t)slots_cap * sizeof(float2), 16);
     if (smem > 200 * 1024) return fail(CFD_ERR_ARG, "chunk too large to stage (%zu bytes)", smem);
     auto kern = k_cheb_step_dw<NB, VPT, KIND, MOM, CH, LAST>;
     struct Cache {
@@ -450,13 +443,13 @@ cfd_status launch_prepare_values_dw(const cfd_matrix *H, double alpha, double be
                                     cudaStream_t stream) {
     const SellView<double> v = sell_view<double>(H);
     if (!v.packed) return fail(CFD_ERR_ARG, "double-word arithmetic needs packed matrix values (CFD_PACK_RI)");
-    if ((size_t)H->n_slots * sizeof(float4) > out_bytes)
+    if ((size_t)H->n_slots * sizeof(float2) > out_bytes)
         return fail(CFD_ERR_ARG, "matrix stores %lld slots, more than the filter workspace prepares (%d per row)",
                     (long long)H->n_slots, kMaxRowSlots);
     const int64_t n_pos = H->n_chunks << v.log2C;
     if (n_pos == 0) return CFD_OK;
     k_prepare_values_dw<<<(unsigned)((n_pos + 255) / 256), 256, 0, stream>>>(v, n_pos, alpha, beta, chunk_rid, rcoef,
-                                                                            rcoef_ld, static_cast<float4 *>(out));
+                                                                            rcoef_ld, static_cast<float2 *>(out));
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     return CFD_OK;

@@ -202,7 +202,7 @@ template <> struct FpTypes<FPM_C64> {
 template <> struct FpTypes<FPM_DW> {
     using T = double;
     using E = float4;
-    using V = float4;     // {hi, s hi, -lo, -s lo}: the slot's packed operands
+    using V = float2;
 };
 
 // VPT consecutive elements (complex float pairs as one 16-byte access).
@@ -548,21 +548,30 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                         s2[q] = make_float2(-wo[q].x, -wo[q].y);
                         e2[q] = make_float2(-wo[q].z, -wo[q].w);
                     }
-                    // a slot's prepared value holds the packed operands
-                    // (hh, nhl), the sign of an imaginary slot included
                     auto madd_re = [&](int kk) {
                         E v[VPT];
                         vrow(kk, v);
-                        const float4 h = val_s[kk * FP_C + rr];
-                        const float2 hh = make_float2(h.x, h.y);
+                        const float2 h = val_s[kk * FP_C + rr];
+                        const float2 hh = make_float2(h.x, h.x);
                         const float2 nhh = neg2(hh);
-                        const float2 nhl = make_float2(h.z, h.w);
+                        const float2 nhl = make_float2(-h.y, -h.y);
 #pragma unroll
                         for (int q = 0; q < VPT; ++q)
                             dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y),
                                     make_float2(v[q].z, v[q].w));
                     };
-                    auto madd_im = madd_re;
+                    auto madd_im = [&](int kk) {
+                        E v[VPT];
+                        vrow(kk, v);
+                        const float2 h = val_s[kk * FP_C + rr];
+                        const float2 hh = make_float2(h.x, -h.x);
+                        const float2 nhh = neg2(hh);
+                        const float2 nhl = make_float2(-h.y, h.y);
+#pragma unroll
+                        for (int q = 0; q < VPT; ++q)
+                            dw_mac2(s2[q], e2[q], hh, nhh, nhl, make_float2(v[q].x, v[q].y),
+                                    make_float2(v[q].z, v[q].w));
+                    };
                     auto swap_acc = [&]() {
 #pragma unroll
                         for (int q = 0; q < VPT; ++q) {
