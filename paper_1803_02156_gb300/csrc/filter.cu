@@ -275,7 +275,7 @@ size_t filter_workspace(int64_t N, int n_s, int n_b, int n_p, int prec_H, int pr
     c.take<double>((size_t)n_p * n_b * 2);                    // raw dots
     c.take<double>((size_t)STEP_MAX_GRID * 2 * n_b);       // CTA partials
     c.take<unsigned>(64);                                     // ticket
-    if (n_b == 32) c.take<char>(footprint_bytes(N, prec_H == CFD_C128 ? 8 : 4));   // chunk footprints
+    if (n_b == 32) c.take<char>(footprint_bytes(N));          // chunk footprints
     return round_up(c.off, 256);
 }
 
@@ -330,8 +330,7 @@ static cfd_status run_filter(const cfd_matrix *H, const FilterPlan &P, const cfd
     if (P.footprint >= 0 && !P.persistent && P.staged >= 1 && ws.fp && (dw || std::is_same<T, float>::value)) {
         int fmax = footprint_rows_cap(H, n_b, vpt, dw, P.footprint > 0);
         if (P.footprint > 0) fmax = std::min(fmax, P.footprint);
-        if (fmax > 0)
-            CFD_TRY(launch_footprint(H, P.chunk_rid, fmax, ws.prep, dw ? 8 : 4, ws.fp, ws.fp_bytes, &F, stream));
+        if (fmax > 0) CFD_TRY(launch_footprint(H, P.chunk_rid, fmax, ws.fp, ws.fp_bytes, &F, stream));
     }
     C *va = static_cast<C *>(ws.va), *vb = static_cast<C *>(ws.vb);
     const int n_blocks = X.n_cols / n_b;
@@ -443,7 +442,7 @@ static FilterScratch carve_filter(const cfd_matrix *H, const cfd_block &X, int n
     ws.raw = c.take<double>((size_t)n_p * n_b * 2);
     ws.partial = c.take<double>((size_t)STEP_MAX_GRID * 2 * n_b);
     ws.ticket = c.take<unsigned>(64);
-    ws.fp_bytes = n_b == 32 ? footprint_bytes(H->n_rows, H->prec == CFD_C128 ? 8 : 4) : 0;
+    ws.fp_bytes = n_b == 32 ? footprint_bytes(H->n_rows) : 0;
     ws.fp = ws.fp_bytes ? c.take<char>(ws.fp_bytes) : nullptr;
     ws.grid_cap = STEP_MAX_GRID;
     return ws;

@@ -125,25 +125,22 @@ cfd_status launch_prepare_values_dw(const cfd_matrix *H, double alpha, double be
 // steps (step_fp.cu): the rows of V_cur each chunk reads, as row ranges
 // staged by TMA into shared memory, and every slot's column as its row there.
 struct FpView {
-    const uint16_t *lcol = nullptr;   // per chunk 32 x 16, row-major: each slot's column as its row in the
-                                      // staged footprint (rows padded with zeros to 16 slots)
-    const void *val = nullptr;        // per chunk 32 x 16, row-major: the slots' prepared values
+    const uint16_t *lcol = nullptr;   // per slot (H's SELL layout): the column's row in the staged footprint
     const int2 *desc = nullptr;       // per chunk 32 words: {chunk_len, ranges (-1: not staged)}, {rows, row of
                                       // the first own row}, first slot, 5 unused, 16 ranges {first row, rows}, 8 unused
     int fmax = 0;                     // footprint rows one stage holds (0: footprint steps off)
 };
-// Workspace bytes of the footprints of an N-row matrix (vbytes per prepared value).
-size_t footprint_bytes(int64_t N, int vbytes);
+// Workspace bytes of the footprints of an N-row matrix.
+size_t footprint_bytes(int64_t N);
 // Footprint rows one stage of the footprint step holds for H at n_b / vpt
 // (complex float, or complex double in double-word arithmetic); 0 when the
 // step does not apply (it needs packed values, C = 32, sigma = 1, n_b = 32)
 // or, unless any_size, when H has too few chunks for it to pay.
 int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw, bool any_size);
-// Builds the footprints of H's chunks (at most fmax rows each) in buf and the
-// row-major copy of the prepared values prep (vbytes each); in a batch
-// (chunk_rid set) each descriptor also names its chunk's realisation.
-cfd_status launch_footprint(const cfd_matrix *H, const int32_t *chunk_rid, int fmax, const void *prep, int vbytes,
-                            void *buf, size_t buf_bytes, FpView *out, cudaStream_t stream);
+// Builds the footprints of H's chunks (at most fmax rows each) in buf; in a
+// batch (chunk_rid set) each descriptor also names its chunk's realisation.
+cfd_status launch_footprint(const cfd_matrix *H, const int32_t *chunk_rid, int fmax, void *buf, size_t buf_bytes,
+                            FpView *out, cudaStream_t stream);
 // One general step with the footprints staged (complex float; complex double
 // in double-word arithmetic, last: X written back as complex double).
 cfd_status launch_step_fp(const StepArgs<float> &A, const FpView &F, int nb, int vpt, int grid_cap, cudaStream_t s);

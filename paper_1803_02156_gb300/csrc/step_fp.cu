@@ -33,8 +33,6 @@ constexpr int FP_RMAX = 16;     // row ranges of a staged footprint
 constexpr int FP_GAP = 4;       // rows two ranges may be apart and still be merged
 constexpr int FP_KEYS = 512;    // slots + own rows of a chunk the builder sorts
 constexpr int FP_C = 32;        // chunk height the footprint steps are built for
-constexpr int FP_LP = 16;       // slots a row holds in the row-major slot arrays (chunk length <= 16)
-constexpr int FP_CS = FP_C * FP_LP;   // entries of one chunk's row-major slot arrays
 // Slots of a chunk whose rows all have six neighbours (Topi, packed values):
 // the on-site entry and 8 real hop entries, 4 imaginary ones.  Chunks of this
 // shape take a fully unrolled row sum (compile-time slot indices, every
@@ -82,10 +80,7 @@ __host__ __device__ inline FpLayout fp_layout(int slots_cap, int val_bytes, int 
 // One CTA per chunk (grid-stride): the chunk's slot columns and own rows are
 // sorted (bitonic, FP_KEYS keys, padding slots and unused keys INT_MAX),
 // runs of keys no more than FP_GAP apart become ranges, and each slot's
-// column is replaced by its row in the concatenated ranges.  The slots'
-// rows (lcol) and their prepared values (val, vbytes each, copied from
-// prep) are written row-major, FP_LP per row padded with zeros, so that a
-// thread reads its row's slots with a few 16-byte loads.  The chunk's
+// column is replaced by its row in the concatenated ranges.  The chunk's
 // descriptor desc[c 32 + l] (32 int2, one coalesced 256-byte load for a
 // warp) holds in word 0 {chunk_len, ranges (-1: not staged)}, word 1
 // {footprint rows, row of the chunk's first own row}, word 2 the chunk's
@@ -93,8 +88,7 @@ __host__ __device__ inline FpLayout fp_layout(int slots_cap, int val_bytes, int 
 // 0}, words 8 + r {first row, rows} of range r.
 __global__ void __launch_bounds__(256) k_footprint(const int32_t *col, const int64_t *chunk_ptr,
                                                    const int32_t *chunk_len, int64_t n_rows, int64_t n_chunks,
-                                                   const int32_t *chunk_rid, int fmax, const void *prep, int vbytes,
-                                                   uint16_t *lcol, void *val, int2 *desc) {
+                                                   const int32_t *chunk_rid, int fmax, uint16_t *lcol, int2 *desc) {
     __shared__ int key[FP_KEYS];
     __shared__ int rs[FP_RMAX], re[FP_RMAX], ro[FP_RMAX];
     __shared__ int s_nr, s_total;
@@ -183,18 +177,9 @@ __global__ void __launch_bounds__(256) k_footprint(const int32_t *col, const int
             else if (tid >= 8 && tid - 8 < nr) d = make_int2(rs[tid - 8], re[tid - 8] - rs[tid - 8]);
             desc[c * 32 + tid] = d;
         }
-        const int len = nslot / FP_C;
-        for (int t = tid; t < FP_CS; t += blockDim.x) {
-            const int rr = t / FP_LP, k = t % FP_LP;
-            const int64_t src = base + (int64_t)k * FP_C + rr;
-            const int cc = k < len ? col[src] : -1;
-            lcol[c * FP_CS + t] = (uint16_t)((nr >= 0 && cc >= 0) ? local(cc) : 0);
-            if (vbytes == 8) {
-                static_cast<uint2 *>(val)[c * FP_CS + t] =
-                    k < len ? static_cast<const uint2 *>(prep)[src] : make_uint2(0u, 0u);
-            } else {
-                static_cast<uint32_t *>(val)[c * FP_CS + t] = k < len ? static_cast<const uint32_t *>(prep)[src] : 0u;
-            }
+        for (int t = tid; t < nslot; t += blockDim.x) {
+            const int cc = col[base + t];
+            lcol[base + t] = (uint16_t)((nr >= 0 && cc >= 0) ? local(cc) : 0);
         }
         __syncthreads();
     }
@@ -312,7 +297,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
     E *wout = reinterpret_cast<E *>(A.w);
     E *xio = reinterpret_cast<E *>(A.x);
     const int64_t ldx = A.ldx;
-    const V *gval = reinterpret_cast<const V *>(F.val);      // row-major prepared values
+    const V *gval = reinterpret_cast<const V *>(A.prep_val);
     const uint32_t tx_extra = A.staged == 2 ? 16u : 0u;
     const long long limit = A.staged == 2 ? (1LL << 24) : (1LL << 32);
     volatile int *abort_flag = &s_abort;
@@ -378,9 +363,8 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                 if (lane >= d) off += t;
             }
             off -= g.y;
-            (void)nslot;
-            const uint32_t bytes = FP_CS * (uint32_t)sizeof(V) + (uint32_t)own * RB * (XST ? 2u : 1u) +
-                                   (nr >= 0 ? FP_CS * 2u + (uint32_t)tot * RB : 0u) + tx_extra;
+            const uint32_t bytes = nslot * (uint32_t)sizeof(V) + (uint32_t)own * RB * (XST ? 2u : 1u) +
+                                   (nr >= 0 ? nslot * 2u + (uint32_t)tot * RB : 0u) + tx_extra;
             if (lane == 0) {
                 s_info[s] = make_int4(cl, nr, own_off, own);
                 // the step's weight g_p c_p (in a batch, that of the chunk's realisation)
@@ -389,8 +373,8 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (lane == 0) mbar_expect_tx(&full[s], bytes);
             __syncwarp();
-            if (lane == 0 && nr >= 0) tma_load_1d(st + L.lcol, F.lcol + c * FP_CS, FP_CS * 2u, &full[s]);
-            if (lane == 1) tma_load_1d(st + L.val, gval + c * FP_CS, FP_CS * (uint32_t)sizeof(V), &full[s]);
+            if (lane == 0 && nr >= 0 && nslot) tma_load_1d(st + L.lcol, F.lcol + base, nslot * 2u, &full[s]);
+            if (lane == 1 && nslot) tma_load_1d(st + L.val, gval + base, nslot * (uint32_t)sizeof(V), &full[s]);
             if (lane == 2) tma_load_1d(st + L.prev, wout + c * FP_C * NB, (uint32_t)own * RB, &full[s]);
             if (XST && lane < own) tma_load_1d(st + L.xs + lane * RB, xio + (c * FP_C + lane) * ldx, RB, &full[s]);
             if (lane < nr)
@@ -484,7 +468,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                 const int64_t i = c * FP_C + rr;
                 auto vrow = [&](int kk, E (&v)[VPT]) {
                     if constexpr (SM) {
-                        lds_row(rows_s + (int)lc_s[rr * FP_LP + kk] * NB, v);
+                        lds_row(rows_s + (int)lc_s[kk * FP_C + rr] * NB, v);
                     } else {
                         const int cc = max(__ldg(A.H.col + gbase + kk * FP_C + rr), 0);   // padding: col -1, value 0
                         ldg_row(vin + (int64_t)cc * NB, v);
@@ -512,7 +496,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                     auto madd_re = [&](int kk) {
                         E v[VPT];
                         vrow(kk, v);
-                        const float h = val_s[rr * FP_LP + kk];
+                        const float h = val_s[kk * FP_C + rr];
 #pragma unroll
                         for (int q = 0; q < VPT; ++q) {
                             acc[q].x = fmaf(h, v[q].x, acc[q].x);
@@ -522,52 +506,14 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                     auto madd_im = [&](int kk) {
                         E v[VPT];
                         vrow(kk, v);
-                        const float h = val_s[rr * FP_LP + kk];
+                        const float h = val_s[kk * FP_C + rr];
 #pragma unroll
                         for (int q = 0; q < VPT; ++q) {
                             acc[q].x = fmaf(-h, v[q].y, acc[q].x);
                             acc[q].y = fmaf(h, v[q].x, acc[q].y);
                         }
                     };
-                    if (SM && nre == FP_FULL_RE && len == FP_FULL_RE + FP_FULL_IM) {
-                        // the row's local columns and values in 16-byte loads
-                        const uint4 *lp = reinterpret_cast<const uint4 *>(lc_s + rr * FP_LP);
-                        const uint4 l0 = lp[0], l1 = lp[1];
-                        const uint32_t lw[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
-                        const float4 *vp = reinterpret_cast<const float4 *>(val_s + rr * FP_LP);
-                        float hv[16];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const float4 f = vp[j];
-                            hv[4 * j] = f.x;
-                            hv[4 * j + 1] = f.y;
-                            hv[4 * j + 2] = f.z;
-                            hv[4 * j + 3] = f.w;
-                        }
-                        auto row_of = [&](int kk) { return (int)((lw[kk >> 1] >> (16 * (kk & 1))) & 0xffffu); };
-                        auto mre = [&](int kk) {
-                            E v[VPT];
-                            lds_row(rows_s + row_of(kk) * NB, v);
-                            const float h = hv[kk];
-#pragma unroll
-                            for (int q = 0; q < VPT; ++q) {
-                                acc[q].x = fmaf(h, v[q].x, acc[q].x);
-                                acc[q].y = fmaf(h, v[q].y, acc[q].y);
-                            }
-                        };
-                        auto mim = [&](int kk) {
-                            E v[VPT];
-                            lds_row(rows_s + row_of(kk) * NB, v);
-                            const float h = hv[kk];
-#pragma unroll
-                            for (int q = 0; q < VPT; ++q) {
-                                acc[q].x = fmaf(-h, v[q].y, acc[q].x);
-                                acc[q].y = fmaf(h, v[q].x, acc[q].y);
-                            }
-                        };
-                        unrolled<0, FP_FULL_RE>(mre);
-                        unrolled<FP_FULL_RE, FP_FULL_RE + FP_FULL_IM>(mim);
-                    } else if (nre == FP_FULL_RE && len == FP_FULL_RE + FP_FULL_IM) {
+                    if (nre == FP_FULL_RE && len == FP_FULL_RE + FP_FULL_IM) {
                         unrolled<0, FP_FULL_RE>(madd_re);
                         unrolled<FP_FULL_RE, FP_FULL_RE + FP_FULL_IM>(madd_im);
                     } else {
@@ -605,7 +551,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                     auto madd_re = [&](int kk) {
                         E v[VPT];
                         vrow(kk, v);
-                        const float2 h = val_s[rr * FP_LP + kk];
+                        const float2 h = val_s[kk * FP_C + rr];
                         const float2 hh = make_float2(h.x, h.x);
                         const float2 nhh = neg2(hh);
                         const float2 nhl = make_float2(-h.y, -h.y);
@@ -617,7 +563,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                     auto madd_im = [&](int kk) {
                         E v[VPT];
                         vrow(kk, v);
-                        const float2 h = val_s[rr * FP_LP + kk];
+                        const float2 h = val_s[kk * FP_C + rr];
                         const float2 hh = make_float2(h.x, -h.x);
                         const float2 nhh = neg2(hh);
                         const float2 nhl = make_float2(-h.y, h.y);
@@ -826,7 +772,7 @@ cfd_status launch_fp_t(const StepArgs<typename FpTypes<MODE>::T> &A, const FpVie
     constexpr int S = FpConf<MODE>::S;
     constexpr bool XST = FpConf<MODE>::XST;
     constexpr int RB = FP_NB * (int)sizeof(typename Ty::E);
-    const int slots_cap = FP_CS;
+    const int slots_cap = A.H.slots_bound * FP_C;
     const FpLayout L = fp_layout(slots_cap, (int)sizeof(typename Ty::V), RB, F.fmax, XST);
     const size_t smem = (size_t)S * L.stage;
     size_t budget = 0;
@@ -875,17 +821,16 @@ cfd_status fp_check(const StepArgs<T> &A, const FpView &F, int nb, int vpt) {
     if (nb != FP_NB) return fail(CFD_ERR_INTERNAL, "footprint step built for n_b = %d", FP_NB);
     if (!A.H.packed || A.H.log2C != 5 || A.H.perm || (A.chunk_rid && !A.rcoef))
         return fail(CFD_ERR_INTERNAL, "footprint step needs a packed C = 32, sigma = 1 matrix");
-    if (A.ldin != FP_NB || A.ldw != FP_NB || !A.x || !A.status || F.fmax <= 0 || !F.lcol || !F.val)
+    if (A.ldin != FP_NB || A.ldw != FP_NB || !A.x || !A.status || !A.prep_val || F.fmax <= 0 || !F.lcol)
         return fail(CFD_ERR_INTERNAL, "footprint step arguments incomplete");
     return CFD_OK;
 }
 
 }  // namespace
 
-size_t footprint_bytes(int64_t N, int vbytes) {
+size_t footprint_bytes(int64_t N) {
     const int64_t n_chunks = (N + FP_C - 1) / FP_C;
-    return round_up((size_t)n_chunks * FP_CS * 2, 256) + round_up((size_t)n_chunks * FP_CS * vbytes, 256) +
-           round_up((size_t)n_chunks * 256, 256);
+    return round_up((size_t)kMaxRowSlots * (size_t)(N + 127) * 2, 256) + round_up((size_t)n_chunks * 256, 256);
 }
 
 int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw, bool any_size) {
@@ -898,27 +843,25 @@ int footprint_rows_cap(const cfd_matrix *H, int nb, int vpt, bool dw, bool any_s
     // SM the gathered steps (several CTAs per SM) are faster
     if (!any_size && H->n_chunks < (int64_t)CFD_FP_MIN_CHUNKS_PER_SM * sm_count()) return 0;
     if (dw ? H->prec != CFD_C128 : H->prec != CFD_C64) return 0;
-    const int cap = dw ? fp_rows_cap_t<FPM_DW>(FP_CS) : fp_rows_cap_t<FPM_C64>(FP_CS);
+    const int cap = dw ? fp_rows_cap_t<FPM_DW>(slots_bound * FP_C) : fp_rows_cap_t<FPM_C64>(slots_bound * FP_C);
     return std::min(cap, 65535);
 }
 
-cfd_status launch_footprint(const cfd_matrix *H, const int32_t *chunk_rid, int fmax, const void *prep, int vbytes,
-                            void *buf, size_t buf_bytes, FpView *out, cudaStream_t stream) {
+cfd_status launch_footprint(const cfd_matrix *H, const int32_t *chunk_rid, int fmax, void *buf, size_t buf_bytes,
+                            FpView *out, cudaStream_t stream) {
     const int64_t n_chunks = (H->n_rows + FP_C - 1) / FP_C;
     if (H->C != FP_C || H->n_chunks != n_chunks) return fail(CFD_ERR_INTERNAL, "footprint needs C = 32");
-    if ((vbytes != 4 && vbytes != 8) || !prep) return fail(CFD_ERR_INTERNAL, "footprint needs the prepared values");
-    if (footprint_bytes(H->n_rows, vbytes) > buf_bytes) return fail(CFD_ERR_INTERNAL, "footprint buffer too small");
+    if (H->n_slots > (int64_t)kMaxRowSlots * (H->n_rows + 127) || footprint_bytes(H->n_rows) > buf_bytes)
+        return fail(CFD_ERR_INTERNAL, "footprint buffer too small");
     Carve c(buf, buf_bytes);
-    uint16_t *lcol = c.take<uint16_t>((size_t)n_chunks * FP_CS);
-    void *val = c.take<char>((size_t)n_chunks * FP_CS * vbytes);
+    uint16_t *lcol = c.take<uint16_t>((size_t)kMaxRowSlots * (size_t)(H->n_rows + 127));
     int2 *desc = c.take<int2>((size_t)n_chunks * 32);
     const int grid = (int)std::min<int64_t>(n_chunks, (int64_t)sm_count() * 8);
     k_footprint<<<grid, 256, 0, stream>>>(H->col, H->chunk_ptr, H->chunk_len, H->n_rows, n_chunks, chunk_rid, fmax,
-                                          prep, vbytes, lcol, val, desc);
+                                          lcol, desc);
     CFD_COUNT_LAUNCH();
     CFD_LAUNCH_CHECK();
     out->lcol = lcol;
-    out->val = val;
     out->desc = desc;
     out->fmax = fmax;
     return CFD_OK;
