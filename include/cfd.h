@@ -562,7 +562,7 @@ size_t cfd_filter_slab_workspace(const cfd_slab *s, int n_s, int n_b, int n_p, i
  * step; mode 1 (pipelined mode, Algorithm 4): all blocks advance one degree
  * at a time and the exchange of block b + 1 runs on a second stream while
  * block b computes.  moments (device, nullable, [n_s][2 n_p]): the moments of
- * the whole vectors (per-slab dots summed).  opts: vpt and arith are used.
+ * the whole vectors (per-slab dots summed).  opts: vpt, arith and footprint are used.
  * Asynchronous on `stream`.
  */
 cfd_status cfd_filter_slabs(int nranks, const cfd_slab *slabs, const cfd_matrix *const *H, double lmin, double lmax,

@@ -745,10 +745,11 @@ def cfd_build_matrix_slab(params, slab, C=32, sigma=1, prec="c128", device="cuda
 
 
 def cfd_filter_slabs(slabs, Hs, lmin, lmax, lam_l, lam_r, n_p, Xs, n_b, mode=CFD_DIST_VECTOR, moments=False,
-                     arith=0, stream=None):
+                     arith=0, stream=None, footprint=0):
     """The distributed filter with every slab in this process (halo exchange by
     device copies).  Xs: the slabs' local blocks (filtered in place).  Returns
-    the moments of the whole vectors when moments=True."""
+    the moments of the whole vectors when moments=True.  footprint: as in
+    cfd_filter_ex."""
     n = len(slabs)
     S = (cfd_slab * n)(*slabs)
     blks = [block_of(X) for X in Xs]
@@ -759,7 +760,7 @@ def cfd_filter_slabs(slabs, Hs, lmin, lmax, lam_l, lam_r, n_p, Xs, n_b, mode=CFD
     works = [_workspace(ws, Xs[0].device) for _ in range(n)]
     W = (ctypes.c_void_p * n)(*[w.data_ptr() for w in works])
     mu = torch.empty(blks[0].n_cols, 2 * n_p, dtype=torch.float64, device=Xs[0].device) if moments else None
-    o = cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0)
+    o = cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0, footprint)
     _check(lib().cfd_filter_slabs(n, S, Hp, lmin, lmax, lam_l, lam_r, n_p, B, n_b, mode, W, ws, _ptr(mu),
                                   ctypes.byref(o), _stream(stream)))
     (stream or torch.cuda.current_stream()).synchronize()      # the workspaces are freed on return
@@ -786,15 +787,16 @@ def cfd_nccl_comm_destroy(comm):
 
 
 def cfd_filter_slab_nccl(slab, H, lmin, lmax, lam_l, lam_r, n_p, X, n_b, comm, mode=CFD_DIST_VECTOR,
-                         moments=False, arith=0, work=None, stream=None):
+                         moments=False, arith=0, work=None, stream=None, footprint=0):
     """One rank's part of the distributed filter (one slab per process and GPU,
-    halo exchange over NCCL).  Every rank receives the global moments."""
+    halo exchange over NCCL).  Every rank receives the global moments.
+    footprint: as in cfd_filter_ex."""
     blk = block_of(X)
     ws = lib().cfd_filter_slab_workspace(ctypes.byref(slab), blk.n_cols, n_b, n_p, H.prec, mode)
     if work is None or work.numel() < ws:
         work = _workspace(ws, X.device)
     mu = torch.empty(blk.n_cols, 2 * n_p, dtype=torch.float64, device=X.device) if moments else None
-    o = cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0)
+    o = cfd_filter_opts(0, 0, 0, 0, 0, 0, arith, 0, footprint)
     _check(lib().cfd_filter_slab_nccl(ctypes.byref(slab), H.ref(), lmin, lmax, lam_l, lam_r, n_p, blk, n_b, mode,
                                       _ptr(work), work.numel(), _ptr(mu), ctypes.byref(o), comm, _stream(stream)))
     return mu

@@ -97,7 +97,7 @@ struct SlabState {
 };
 
 struct SlabLayout {
-    size_t prep, raw, vbuf, total;
+    size_t prep, raw, vbuf, fp, total;
     int n_vpairs;
 };
 
@@ -109,6 +109,7 @@ SlabLayout slab_layout(const cfd_slab &s, int n_s, int n_b, int n_p, int prec, i
     L.prep = (size_t)kMaxRowSlots * (size_t)(s.n_local + 127) * sH;
     L.raw = (size_t)(mode == 1 ? n_blocks : 1) * n_p * n_b * 2;
     L.vbuf = (size_t)(s.n_local + 2 * s.plane) * n_b * sH;
+    L.fp = n_b == 32 ? footprint_bytes(s.n_local) : 0;      // chunk footprints of the slab's rows
     Carve c(nullptr, 0);
     c.take<int>(64);
     c.take<char>(L.prep);
@@ -117,6 +118,7 @@ SlabLayout slab_layout(const cfd_slab &s, int n_s, int n_b, int n_p, int prec, i
     c.take<unsigned>(64);
     c.take<double>(L.raw);
     for (int k = 0; k < 2 * L.n_vpairs; ++k) c.take<char>(L.vbuf);
+    if (L.fp) c.take<char>(L.fp);
     L.total = round_up(c.off, 256);
     return L;
 }
@@ -219,6 +221,7 @@ struct DistArgs {
     double lmin, lmax, lam_l, lam_r;
     int n_p, n_b, mode, arith, vpt;
     double *moments;
+    int footprint;       // as cfd_filter_opts.footprint
 };
 
 template <typename T>
@@ -231,6 +234,7 @@ cfd_status run_dist(std::vector<SlabState> &S, Exchanger &ex, const DistArgs &D,
     const bool dw = std::is_same<T, double>::value && D.arith == ARITH_DW && n_p >= 3;
     const int vpt = D.vpt > 0 ? D.vpt : default_vpt(S[0].H->prec, n_b);
     std::vector<StepArgs<T>> A(S.size());
+    std::vector<FpView> F(S.size());     // the general steps' footprints, per slab (fmax 0: gathered steps)
     for (size_t r = 0; r < S.size(); ++r) {
         SlabState &st = S[r];
         CFD_CUDA(cudaMemsetAsync(st.ws.ticket, 0, sizeof(unsigned), stream));
@@ -252,10 +256,22 @@ cfd_status run_dist(std::vector<SlabState> &S, Exchanger &ex, const DistArgs &D,
         a.gather = default_gather(st.H->prec);
         a.status = st.ws.status;
         a.prep_val = st.ws.prep;
+        // the footprint-staged general steps: a slab row's halo columns are
+        // rows of the recurrence buffers past n_local, so footprints reach them
+        if (D.footprint >= 0 && st.ws.fp && (dw || std::is_same<T, float>::value)) {
+            int fmax = footprint_rows_cap(st.H, n_b, vpt, dw, D.footprint > 0);
+            if (D.footprint > 0) fmax = std::min(fmax, D.footprint);
+            if (fmax > 0) CFD_TRY(launch_footprint(st.H, nullptr, fmax, st.ws.fp, st.ws.fp_bytes, &F[r], stream));
+        }
     }
     auto step = [&](size_t r, int kind, int p, bool last, cudaStream_t s) -> cfd_status {
+        (void)p;
         if constexpr (std::is_same<T, double>::value) {
+            if (dw && kind == STEP_GENERAL && F[r].fmax > 0)
+                return launch_step_fp_dw(A[r], F[r], n_b, vpt, last, STEP_MAX_GRID, s);
             if (dw) return launch_step_dw(kind, n_b, vpt, A[r], last, STEP_MAX_GRID, s);
+        } else {
+            if (kind == STEP_GENERAL && F[r].fmax > 0) return launch_step_fp(A[r], F[r], n_b, vpt, STEP_MAX_GRID, s);
         }
         return launch_step<T>(kind, n_b, vpt, A[r], STEP_MAX_GRID, s);
     };
@@ -406,6 +422,8 @@ cfd_status setup_states(std::vector<SlabState> &S, int n, const cfd_slab *slabs,
             st.va[k] = c.take<char>(L.vbuf);
             st.vb[k] = c.take<char>(L.vbuf);
         }
+        st.ws.fp_bytes = L.fp;
+        st.ws.fp = L.fp ? c.take<char>(L.fp) : nullptr;
         st.ws.grid_cap = STEP_MAX_GRID;
     }
     return CFD_OK;
@@ -444,7 +462,9 @@ cfd_status cfd_filter_slabs(int nranks, const cfd_slab *slabs, const cfd_matrix 
     std::vector<SlabState> S;
     CFD_TRY(setup_states(S, nranks, slabs, H, X, n_p, n_b, mode, work, work_bytes));
     LocalExchanger ex;
-    DistArgs D{lmin, lmax, lam_l, lam_r, n_p, n_b, mode, arith, opts ? opts->vpt : 0, moments};
+    if (opts && opts->footprint < -1) return fail(CFD_ERR_ARG, "footprint=%d < -1", opts->footprint);
+    DistArgs D{lmin, lmax, lam_l, lam_r, n_p, n_b, mode, arith, opts ? opts->vpt : 0, moments,
+               opts ? opts->footprint : 0};
     return dist_filter(S, ex, D, stream);
 }
 
@@ -491,7 +511,9 @@ cfd_status cfd_filter_slab_nccl(const cfd_slab *slab, const cfd_matrix *H, doubl
     void *w[1] = {work};
     CFD_TRY(setup_states(S, 1, slab, &H, &X, n_p, n_b, mode, w, work_bytes));
     NcclExchanger ex(api, comm);
-    DistArgs D{lmin, lmax, lam_l, lam_r, n_p, n_b, mode, arith, opts ? opts->vpt : 0, moments};
+    if (opts && opts->footprint < -1) return fail(CFD_ERR_ARG, "footprint=%d < -1", opts->footprint);
+    DistArgs D{lmin, lmax, lam_l, lam_r, n_p, n_b, mode, arith, opts ? opts->vpt : 0, moments,
+               opts ? opts->footprint : 0};
     return dist_filter(S, ex, D, stream);
 }
 

@@ -130,3 +130,29 @@ def test_filter_slab_nccl_single_rank(b, mode, arith):
     b.cfd_nccl_comm_destroy(comm)
     assert torch.equal(X, ref)
     assert (torch.max(torch.abs(mu - mu_ref)) / torch.max(torch.abs(mu_ref))).item() < 1e-13
+
+
+@pytest.mark.parametrize("L,per_z,nranks", [((8, 8, 6), 0, 2), ((8, 4, 7), 1, 3)])
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("prec,arith", [("c128p", 1), ("c64p", 0)])
+def test_filter_slabs_footprint_equals_whole_matrix(b, L, per_z, nranks, mode, prec, arith):
+    """The slabs with the footprint-staged general steps (forced at this size;
+    the footprints reach into the halo rows) against the whole matrix with
+    the gathered steps: bit for bit."""
+    import torch
+    per = (1, 1, per_z)
+    n_s, n_b, n_p, win = 32, 32, 25, (-0.6, 0.4)
+    dt = torch.complex64 if prec.startswith("c64") else torch.complex128
+    p = b.topi_params(*L, periodic=per)
+    H = b.cfd_build_matrix(p, 32, 1, prec)
+    X0 = torch.from_numpy(inputs.gaussian_block(H.N, n_s, seed=7)).to(dt).cuda()
+    ref = X0.clone()
+    mu_ref = b.cfd_filter_ex(H, -8.6, 8.6, win[0], win[1], n_p, ref, n_b, moments=True, arith=arith, footprint=-1)
+    slabs = [b.cfd_slab_plan(p, nranks, r) for r in range(nranks)]
+    Hs = [b.cfd_build_matrix_slab(p, s, 32, 1, prec) for s in slabs]
+    Xs = [X0[s.row0:s.row0 + s.n_local].clone() for s in slabs]
+    mu = b.cfd_filter_slabs(slabs, Hs, -8.6, 8.6, win[0], win[1], n_p, Xs, n_b, mode=mode, moments=True,
+                            arith=arith, footprint=65535)
+    assert torch.equal(torch.cat(Xs, dim=0), ref)
+    tol = 1e-13 if prec.startswith("c128") else 1e-5
+    assert (torch.max(torch.abs(mu - mu_ref)) / torch.max(torch.abs(mu_ref))).item() < tol
