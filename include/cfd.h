@@ -358,10 +358,11 @@ cfd_status cfd_filter_host_ex(const cfd_matrix *H, double lmin, double lmax, dou
  * cfd_filter_host_ex for a search space stored block after block in host
  * memory (block b of n_b columns, N rows of n_b complex values, at
  * X.ptr + b N n_b scalars; X.n_rows = N, X.n_cols = n_s, X.ld = n_b): each
- * block moves over the link as one contiguous DMA copy on `stream`, before
- * and after its filter (kernels that fill the SMs starve copies running
- * beside them, so the blocks move at the link's full rate while nothing else
- * runs).  Results equal cfd_filter's on the same columns bit for bit.
+ * block moves over the link as one contiguous copy.  Up to n_p = 40 block
+ * b + 1 comes in and b - 1 goes out while b is filtered (gathered steps);
+ * above it each block's DMA copies run on `stream` before and after its
+ * filter (footprint-staged steps, which starve copies running beside them).
+ * Results equal cfd_filter's on the same columns bit for bit.
  */
 cfd_status cfd_filter_host_blocked(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
                                    int n_p, cfd_block X, int n_b, void *work, size_t work_bytes, double *moments,

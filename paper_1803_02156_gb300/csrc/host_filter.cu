@@ -108,14 +108,18 @@ extern "C" size_t cfd_filter_host_workspace(int64_t N, int n_s, int n_b, int n_p
 #ifndef CFD_HOST_BLOCKED_KERNEL
 #define CFD_HOST_BLOCKED_KERNEL 1
 #endif
-// Schedule of a block-after-block search space: 0 overlapped (block b + 1
-// comes in and b - 1 goes out on the copy stream while b is filtered), 1
-// serial (each block's DMA copies on the filter's own stream, before and
-// after its filter, at the link's full rate).  Next to the footprint-staged
-// steps the overlapped copies are starved to a few GB/s, so moving the
-// blocks while nothing else runs costs less.
-#ifndef CFD_HOST_SERIAL
-#define CFD_HOST_SERIAL 1
+// Schedule of a block-after-block search space.  Overlapped: block b + 1
+// comes in and b - 1 goes out on the copy stream while b is filtered with
+// the gathered steps (several CTAs per SM leave room for the copy kernel).
+// Serial: each block's DMA copies on the filter's own stream, before and
+// after its filter, at the link's full rate, and the footprint-staged
+// steps, next to which overlapped copies are starved.  At low degree the
+// copies dominate and overlapping them pays; at high degree the faster
+// steps do.  Degrees up to CFD_HOST_OVERLAP_MAX_NP take the overlapped
+// schedule (measured on 200x200x100, 16 blocks: n_p = 5 and 20 overlapped
+// 3.2 and 7.6 s against 6.3 and 8.8 s serial; n_p = 100 24.5 against 20.3 s).
+#ifndef CFD_HOST_OVERLAP_MAX_NP
+#define CFD_HOST_OVERLAP_MAX_NP 40
 #endif
 
 static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax, double lam_l, double lam_r,
@@ -161,7 +165,8 @@ static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax
     const int n_blocks = X.n_cols / n_b;
     char *host = static_cast<char *>(X.ptr);
 
-    if (blocked && CFD_HOST_SERIAL) {
+    const bool serial = blocked && n_p > CFD_HOST_OVERLAP_MAX_NP;
+    if (serial) {
         const size_t block_bytes = (size_t)N * width;
         for (int b = 0; b < n_blocks; ++b) {
             CFD_CUDA(cudaMemcpyAsync(dbuf[0], host + (size_t)b * block_bytes, block_bytes, cudaMemcpyHostToDevice,
@@ -208,7 +213,8 @@ static cfd_status filter_host_impl(const cfd_matrix *H, double lmin, double lmax
         D.ld = n_b;
         D.n_cols = n_b;
         CFD_TRY(filter_impl_opts(H, lmin, lmax, lam_l, lam_r, n_p, D, n_b, 0, 0, 0, 0, work, fws,
-                                 moments ? moments + (int64_t)b * n_b * 2 * n_p : nullptr, stream, 0, 0, arith));
+                                 moments ? moments + (int64_t)b * n_b * 2 * n_p : nullptr, stream, 0, 0, arith, 0,
+                                 -1));
         CFD_CUDA(cudaEventRecord(cp.done[b & 1], stream));
         // write block b back, then reuse its buffer for block b + 2
         CFD_CUDA(cudaStreamWaitEvent(cp.copy, cp.done[b & 1], 0));
