@@ -459,7 +459,7 @@ def run_filter(a):
         roof = {"bound": "hbm", "achieved": round(gbs_launch, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(gbs_launch / hbm, 4), "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": hbm_src,
-                "kernel": ("k_cheb_step_fp<complex float,%d,2,moments,4 stages,16+1 warps>" % n_b if fp_on else
+                "kernel": ("k_cheb_step_fp<complex float,%d,4,moments,4 stages,2x8+1 warps>" % n_b if fp_on else
                            "k_cheb_step_staged<float,%d,2,moments,%s>" % (n_b, a.storage)),
                 "algorithmic": "nnz (8 + 4) + 5 N n_b 8 bytes per launch",
                 "avg_launch_ms": round(1e3 * t_launch, 4)}

@@ -38,6 +38,11 @@ constexpr int FP_C = 32;        // chunk height the footprint steps are built fo
 // shape take a fully unrolled row sum (compile-time slot indices, every
 // shared-memory load of the row issued before its multiply-adds).
 constexpr int FP_FULL_RE = 9, FP_FULL_IM = 4;
+// Whether a thread loads its X row of its next chunk while it computes this
+// one (where each thread has one row per chunk and X is not staged).
+#ifndef CFD_FP_XPRE
+#define CFD_FP_XPRE 1
+#endif
 
 // fn(K0), fn(K0 + 1), ..., fn(K1 - 1) with compile-time indices.
 template <int K0, int K1, typename Fn>
@@ -264,7 +269,7 @@ __device__ __forceinline__ void st_elems(E *p, const E (&v)[VPT]) {
 // CFD_ERR_TIMEOUT in *A.status (with CFD_STATUS_DRAIN_EXPIRED if that wait
 // expired too), and the CTA returns without its moments.  A.staged == 2 is
 // the test of that path (every stage expects 16 bytes more than are copied).
-template <int MODE, int NB, int VPT, bool MOM, bool LAST, int S, bool XST, int W>
+template <int MODE, int NB, int VPT, bool MOM, bool LAST, int S, bool XST, int W, int CGT>
 __global__ void __launch_bounds__((W + 1) * 32, 1)
 k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int slots_cap) {
     using E = typename FpTypes<MODE>::E;
@@ -278,6 +283,14 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
     constexpr int TPR = NB / VPT;
     constexpr int RPW = 32 / TPR;
     constexpr int ROWS_PASS = W * RPW;
+    // consumer groups: the warps split into CG groups of WG warps and group g
+    // computes the CTA's chunks j = g (mod CG), each chunk's rows GROUP_PASS
+    // at a time (CGT = 0: as many groups as the warps' rows fill chunks)
+    constexpr int CG = CGT > 0 ? CGT : (ROWS_PASS > FP_C ? ROWS_PASS / FP_C : 1);
+    constexpr int WG = W / CG;
+    constexpr int GROUP_PASS = WG * RPW;
+    static_assert(W % CG == 0 && S % CG == 0 && GROUP_PASS <= FP_C && FP_C % GROUP_PASS == 0,
+                  "bad consumer groups");
     constexpr int RB = NB * (int)sizeof(E);
     static_assert(TPR >= 1 && TPR <= 32 && (32 % TPR) == 0, "bad thread split");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -311,7 +324,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], W);
+            mbar_init(&empty[s], WG);
         }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -445,8 +458,9 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
         // staged footprint (else, for an unstaged chunk, from global memory)
         // one row per thread and chunk, X not staged: each thread loads its X
         // row of the next chunk while it computes this one
-        constexpr bool XPRE = !XST && ROWS_PASS == FP_C;
-        const int my_rr = warp * RPW + sub;
+        constexpr bool XPRE = CFD_FP_XPRE && !XST && GROUP_PASS == FP_C;
+        const int grp = warp / WG;
+        const int my_rr = (warp % WG) * RPW + sub;
         auto x_row_exists = [&](int64_t c) { return c < n_chunks && c * FP_C + my_rr < n_rows; };
         E xpre[VPT];
         auto rows = [&](auto sm_tag, int64_t c, int s, const E (&xin)[VPT]) {
@@ -455,6 +469,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
             const int cl = inf.x, own_off = inf.z, own = inf.w;
             const float4 wv = s_w[s];
             const float g0 = wv.x, gh = wv.y, gl = wv.z;
+            (void)g0, (void)gh, (void)gl;
             const int nre = cl & 0xffff, len = nre + (cl >> 16);
             const unsigned char *st = smem_raw + (size_t)s * L.stage;
             const uint16_t *lc_s = reinterpret_cast<const uint16_t *>(st + L.lcol);
@@ -464,7 +479,7 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
             (void)x_s;
             const E *rows_s = reinterpret_cast<const E *>(st + L.rows);
             const int64_t gbase = SM ? 0 : __ldg(A.H.chunk_ptr + c);
-            for (int rr = warp * RPW + sub; rr < own; rr += ROWS_PASS) {
+            for (int rr = my_rr; rr < own; rr += GROUP_PASS) {
                 const int64_t i = c * FP_C + rr;
                 auto vrow = [&](int kk, E (&v)[VPT]) {
                     if constexpr (SM) {
@@ -624,15 +639,16 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
                 }
             }
         };
-        if (XPRE && x_row_exists(first)) lds_row(xio + (first * FP_C + my_rr) * ldx, xpre);
-        int k = 0;
-        for (int64_t c = first; c < n_chunks; c += stride, ++k) {
+        const int64_t gfirst = first + grp * stride;
+        if (XPRE && x_row_exists(gfirst)) lds_row(xio + (gfirst * FP_C + my_rr) * ldx, xpre);
+        int k = grp;
+        for (int64_t c = gfirst; c < n_chunks; c += CG * stride, k += CG) {
             if (__any_sync(0xffffffffu, *abort_flag)) break;
             const int s = k % S;
             E xcur[VPT];
 #pragma unroll
             for (int q = 0; q < VPT; ++q) xcur[q] = xpre[q];
-            if (XPRE && x_row_exists(c + stride)) lds_row(xio + ((c + stride) * FP_C + my_rr) * ldx, xpre);
+            if (XPRE && x_row_exists(c + CG * stride)) lds_row(xio + ((c + CG * stride) * FP_C + my_rr) * ldx, xpre);
             const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / S) & 1), limit);
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0) *abort_flag = 1;
@@ -688,17 +704,24 @@ k_cheb_step_fp(const StepArgs<typename FpTypes<MODE>::T> A, const FpView F, int 
 #endif
 // Vectors per thread, and consumer warps of the CTA (one CTA per SM, plus
 // the producer warp; 0: one row per thread and chunk, n_b / vpt warps).
+// Complex float: 4 vectors per thread in 16 warps, two groups of 8 warps
+// taking alternate chunks (fewer shared-memory loads of slot columns and
+// values per row than 2 vectors per thread, and as many warps).
 #ifndef CFD_FP_C64_VPT
-#define CFD_FP_C64_VPT 2
+#define CFD_FP_C64_VPT 4
 #endif
 #ifndef CFD_FP_DW_VPT
 #define CFD_FP_DW_VPT 2
 #endif
 #ifndef CFD_FP_C64_WARPS
-#define CFD_FP_C64_WARPS 0
+#define CFD_FP_C64_WARPS 16
 #endif
 #ifndef CFD_FP_DW_WARPS
 #define CFD_FP_DW_WARPS 0
+#endif
+// Consumer groups (0: as many as the warps' rows fill chunks).
+#ifndef CFD_FP_C64_GROUPS
+#define CFD_FP_C64_GROUPS 0
 #endif
 
 namespace {
@@ -711,12 +734,14 @@ template <> struct FpConf<FPM_C64> {
     static constexpr bool XST = CFD_FP_C64_XST != 0;
     static constexpr int VPT = CFD_FP_C64_VPT;
     static constexpr int W = CFD_FP_C64_WARPS ? CFD_FP_C64_WARPS : FP_NB / VPT;
+    static constexpr int CG = CFD_FP_C64_GROUPS;
 };
 template <> struct FpConf<FPM_DW> {
     static constexpr int S = CFD_FP_DW_STAGES;
     static constexpr bool XST = false;
     static constexpr int VPT = CFD_FP_DW_VPT;
     static constexpr int W = CFD_FP_DW_WARPS ? CFD_FP_DW_WARPS : FP_NB / VPT;
+    static constexpr int CG = 0;
 };
 
 // Dynamic shared memory a CTA may take next to the kernel's static shared
@@ -738,9 +763,9 @@ cfd_status fp_smem_budget(size_t *out) {
         // the moments variant carries the reduction's static arrays
         cudaFuncAttributes fa{};
         constexpr int W = FpConf<MODE>::W;
-        CFD_CUDA(cudaFuncGetAttributes(&fa, k_cheb_step_fp<MODE, FP_NB, FpConf<MODE>::VPT, true, false, S, XST, W>));
+        CFD_CUDA(cudaFuncGetAttributes(&fa, k_cheb_step_fp<MODE, FP_NB, FpConf<MODE>::VPT, true, false, S, XST, W, FpConf<MODE>::CG>));
         cudaFuncAttributes fb{};
-        CFD_CUDA(cudaFuncGetAttributes(&fb, k_cheb_step_fp<MODE, FP_NB, FpConf<MODE>::VPT, true, true, S, XST, W>));
+        CFD_CUDA(cudaFuncGetAttributes(&fb, k_cheb_step_fp<MODE, FP_NB, FpConf<MODE>::VPT, true, true, S, XST, W, FpConf<MODE>::CG>));
         const size_t stat = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
         cache[dev] = (size_t)optin > stat + 1024 ? (size_t)optin - stat - 1024 : 1;
     }
@@ -779,7 +804,7 @@ cfd_status launch_fp_t(const StepArgs<typename FpTypes<MODE>::T> &A, const FpVie
     CFD_TRY(fp_smem_budget<MODE>(&budget));
     if (smem > budget) return fail(CFD_ERR_ARG, "footprint stages of %d rows need %zu bytes of shared memory", F.fmax, smem);
     constexpr int W = FpConf<MODE>::W;
-    auto kern = k_cheb_step_fp<MODE, FP_NB, FpConf<MODE>::VPT, MOM, LAST, S, XST, W>;
+    auto kern = k_cheb_step_fp<MODE, FP_NB, FpConf<MODE>::VPT, MOM, LAST, S, XST, W, FpConf<MODE>::CG>;
     struct Cache {
         std::mutex mu;
         int occ[64];
