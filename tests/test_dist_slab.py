@@ -192,7 +192,7 @@ def _worker(rank, world, port, L, per, n_s, n_b, n_p, win, pipelined, out):
 def test_distributed_filter_gloo(world, L, per_z, pipelined):
     per = (1, 1, per_z)
     n_s, n_b, n_p, win = 16, 8, 30, (-0.6, 0.4)
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), L, per, n_s, n_b, n_p, win, pipelined, out), nprocs=world,
              join=True)

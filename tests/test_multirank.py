@@ -29,7 +29,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_timing_and_replica_seeds():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     assert out[0][0] == out[1][0] == 2.0
