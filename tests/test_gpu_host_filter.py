@@ -59,12 +59,15 @@ def test_host_filter_vs_oracle(b, prec, tol):
     assert merr < tol, merr
 
 
-@pytest.mark.parametrize("prec,arith,pinned", [("c128p", 1, True), ("c128p", 0, False), ("c64p", 0, True)])
-def test_host_filter_blocked_equals_device_filter(b, prec, arith, pinned):
+@pytest.mark.parametrize("prec,arith,pinned,n_p", [("c128p", 1, True, 30), ("c128p", 0, False, 30), ("c64p", 0, True, 30),
+                                                   ("c128p", 1, True, 50), ("c64p", 0, False, 50)])
+def test_host_filter_blocked_equals_device_filter(b, prec, arith, pinned, n_p):
     """A search space stored block after block in host memory (one contiguous
-    copy per block) gives the device filter's block and moments bit for bit."""
+    copy per block) gives the device filter's block and moments bit for bit,
+    with the overlapped copies of low degrees (n_p = 30) and the serial
+    copies of high degrees (n_p = 50)."""
     import torch
-    L, n_s, n_b, n_p = (12, 10, 7), 64, 16, 30
+    L, n_s, n_b = (12, 10, 7), 64, 16
     H = b.cfd_build_matrix(b.topi_params(*L, seed=1), 32, 1, prec)
     dt = torch.complex64 if prec.startswith("c64") else torch.complex128
     X = torch.from_numpy(inputs.gaussian_block(H.N, n_s, seed=2)).to(dt)
